@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Throughput of the MRT FD-LB step (arXiv:1106.0785) on GB300.
+
+Default workload: Richtmyer-Meshkov, 4096 x 1024 nodes, FP32 distributions
+with FP64 temperature recovery (a Mach-1.5 shock onto a cosine-perturbed
+light/heavy interface; seeded synthetic fields).  One bench step = one time
+step of the whole path: ghost-layer fill + fused step kernel (macroscopic
+recovery, velocity gradients, moments, equilibria, modified collision,
+Lax-Wendroff advection, forward-Euler update).
+
+Printed JSON line (rank 0):
+  value      MLUPS (million lattice-node updates / s), whole job, inputs
+             resident in HBM, CUDA events on the library's stream
+  e2e        the same through the C ABI with host buffers: every step copies
+             f in from pinned host memory and rho, u, T back
+  roofline   step kernel: algorithmic 128 B / node update (16 FP32 reads +
+             16 writes) / its mean launch time, against measured HBM copy
+             bandwidth
+  fp64_mlups the all-FP64 path on the same input
+  cpu_baseline  the FP64 numpy oracle on a crop of the same input, one thread
+
+Multi-GPU (torchrun): every rank advances its own replica (weak scaling, no
+data-path collective); the max time over ranks is reported.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 4096, 1024
+BYTES_PER_LUP_FP32 = 128
+CROP = (1600, 0, 512, 128)      # x0, y0, nx, ny of the CPU-baseline crop
+REF_CROP = (1900, 0, 128, 64)   # per-step sample of the reference arm
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=30)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (one process per GPU; replicas)
+# ---------------------------------------------------------------------------
+def dist_init(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("step_tiled.cu", "physics.cuh", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1106_0785_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "step_tiled_fp32_rm4096x1024.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a crop of the same input
+# ---------------------------------------------------------------------------
+def _crop_problem(crop):
+    import numpy as np
+
+    from oracle import equilibrium as oeq
+    from oracle import fdlb
+    from paper_1106_0785_gb300 import workloads
+
+    cfg, (rho, ux, uy, T) = workloads.richtmyer_meshkov(nx=NX, ny=NY)
+    x0, y0, nx, ny = crop
+    sl = (slice(y0, y0 + ny), slice(x0, x0 + nx))
+    p = fdlb.Params(nx=nx, ny=ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt, s=np.asarray(cfg.s),
+                    sides=(fdlb.Side(fdlb.OUTFLOW), fdlb.Side(fdlb.OUTFLOW), fdlb.Side(), fdlb.Side()))
+    return p, oeq.feq(rho[sl], ux[sl], uy[sl], T[sl])
+
+
+def cpu_baseline_worker(seconds):
+    from oracle import fdlb
+    p, f = _crop_problem(CROP)
+    f = fdlb.step(f, p)  # warm-up
+    n, t0 = 0, time.perf_counter()
+    while True:
+        f = fdlb.step(f, p)
+        n += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and n >= 3) or n >= 100000:
+            break
+    print(json.dumps({"steps": n, "seconds": el, "nodes": p.nx * p.ny}))
+
+
+def cpu_baseline(seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = "import bench; bench.cpu_baseline_worker(%r)" % seconds
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    mlups = d["nodes"] * d["steps"] / d["seconds"] / 1e6
+    x0, y0, nx, ny = CROP
+    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "FP64 numpy oracle, %d steps of a %dx%d crop (x %d-%d, y %d-%d) of the "
+                      "Richtmyer-Meshkov 4096x1024 initial state, one thread, %.1f s"
+                      % (d["steps"], nx, ny, x0, x0 + nx - 1, y0, y0 + ny - 1, d["seconds"])}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import fdlb
+    p, f = _crop_problem(REF_CROP)
+    for _ in range(args.warmup):
+        f = fdlb.step(f, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = fdlb.step(f, p)
+    el = time.perf_counter() - t0
+    mlups = p.nx * p.ny * args.steps / el / 1e6
+    x0, y0, nx, ny = REF_CROP
+    sample = ("FP64 numpy oracle, one time step of a %dx%d crop (x %d-%d, y %d-%d) of the "
+              "Richtmyer-Meshkov 4096x1024 initial state per bench step" % (nx, ny, x0, x0 + nx - 1, y0, y0 + ny - 1))
+    line = {
+        "impl": "reference", "metric": "MLUPS, FP32 forward step (Richtmyer-Meshkov 4096x1024)",
+        "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "richtmyer_meshkov_4096x1024", "sample": sample},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_mine(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1106_0785_gb300 import mrtlb as M
+    from paper_1106_0785_gb300 import workloads
+    from paper_1106_0785_gb300.simulation import Simulation
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg, fields = workloads.richtmyer_meshkov(nx=NX, ny=NY, precision="fp32")
+    nodes = NX * NY
+    sim = Simulation(cfg, device=dev)
+    sim.init_equilibrium(*fields)
+    stream = sim.stream
+    sim.step(args.warmup)
+    sim.sync()
+
+    # ---- timed region: K steps, inputs resident in HBM --------------------
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    M.mrtlb_timing_begin(sim.ctx, args.steps)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    kms, nlaunch = M.mrtlb_timing_end(sim.ctx)
+    clocks = clk.stop()
+    sim.sync()  # surfaces any non-physical state met during the run
+    ms_max = max_over_ranks(ms, world, dev)
+    value = world * nodes * args.steps / (ms_max / 1e3) / 1e6
+    launches = M.mrtlb_launches_per_step(sim.ctx) * args.steps
+
+    # ---- roofline of the step kernel --------------------------------------
+    peak, peak_src = measured_peaks()
+    kavg_s = kms / 1e3 / max(nlaunch, 1)
+    achieved = BYTES_PER_LUP_FP32 * nodes / kavg_s / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "step_tiled_kernel<float,128,6>", "kernel_ms_mean": kavg_s * 1e3,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy)"}
+
+    # ---- e2e through the C ABI with host buffers ---------------------------
+    f_host = torch.empty((16, NY, NX), dtype=torch.float32, pin_memory=True)
+    sim.get_f()  # warm the staging buffer
+    M.mrtlb_get_f(sim.ctx, f_host.data_ptr(), 0)
+    outs = [torch.empty((NY, NX), dtype=torch.float64, pin_memory=True) for _ in range(4)]
+    ke = max(1, args.e2e_steps)
+    for _ in range(2):
+        M.mrtlb_set_f(sim.ctx, f_host.data_ptr(), 0)
+        M.mrtlb_step(sim.ctx, 1)
+        M.mrtlb_macros(sim.ctx, *[o.data_ptr() for o in outs], 0)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        M.mrtlb_set_f(sim.ctx, f_host.data_ptr(), 0)      # H2D of f^n (pinned)
+        M.mrtlb_step(sim.ctx, 1)
+        M.mrtlb_macros(sim.ctx, *[o.data_ptr() for o in outs], 0)  # D2H of rho, u, T
+    torch.cuda.synchronize(dev)
+    el = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": world * nodes * ke / el / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": int(f_host.numel() * 4),
+           "d2h_bytes_per_step": int(sum(o.numel() for o in outs) * 8)}
+    sim.close()
+
+    # ---- the all-FP64 path on the same input --------------------------------
+    cfg64, _ = workloads.richtmyer_meshkov(nx=NX, ny=NY, precision="fp64")
+    sim64 = Simulation(cfg64, device=dev)
+    sim64.init_equilibrium(*fields)
+    sim64.step(3)
+    sim64.sync()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(sim64.stream)
+    sim64.step(args.fp64_steps)
+    a1.record(sim64.stream)
+    torch.cuda.synchronize(dev)
+    ms64 = max_over_ranks(a0.elapsed_time(a1), world, dev)
+    sim64.sync()
+    sim64.close()
+    fp64_mlups = world * nodes * args.fp64_steps / (ms64 / 1e3) / 1e6
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "MLUPS, FP32 forward step (Richtmyer-Meshkov 4096x1024)",
+        "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "richtmyer_meshkov_4096x1024", "nx": NX, "ny": NY,
+                   "precision": "fp32 storage, fp64 temperature recovery",
+                   "l2": "inputs larger than L2 (268 MB per f copy)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "fp64_mlups": fp64_mlups,
+        "fp64_ms_per_step": ms64 / args.fp64_steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        world, rank, _ = dist_init("gloo")
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_init("nccl")
+    run_mine(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

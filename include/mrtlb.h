@@ -1,0 +1,177 @@
+/*
+ * mrtlb.h - C ABI of the GB300 implementation of the MRT finite-difference
+ * lattice Boltzmann (FD-LB) model for compressible flow of Chen, Xu, Zhang &
+ * Li, "Prandtl number effects in MRT lattice Boltzmann models for shocked and
+ * unshocked compressible fluids" (arXiv:1106.0785).
+ *
+ * The model (Sec. II): sixteen discrete velocities v_i (Fig. 1), moments
+ * f^ = M f with the SO(2) matrix M, collision -M^-1 S^ (f^ - f^eq) with the
+ * equilibria of Eqs. 14a-14i, and the modified energy-flux relaxation for
+ * moments 7 and 8 (the two rules following Eq. 16c).  The space-time scheme
+ * is the one whose amplification matrix G is given in Sec. III: forward Euler
+ * in time and a Lax-Wendroff difference along each axis.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an mrtlb_status (0 = MRTLB_OK).  mrtlb_last_error()
+ *   gives a human-readable message for the last failure on a context.
+ * - Arrays on the host are borrowed for the duration of the call only.
+ * - Device state buffers are owned by the caller (e.g. PyTorch tensors) and
+ *   must outlive the context; the context owns only its own small scratch
+ *   (staging for host copies, reduction accumulators, the error word), which
+ *   mrtlb_destroy frees.
+ * - Work is enqueued on the context's CUDA stream (params.stream, NULL = the
+ *   legacy default stream).  mrtlb_step is asynchronous; a non-physical state
+ *   (rho <= 0, T <= 0 or a non-finite value) met by a kernel is latched in a
+ *   device error word and reported as MRTLB_ERR_NONPHYSICAL by the next
+ *   synchronising call (mrtlb_macros, mrtlb_get_f, mrtlb_reduce,
+ *   mrtlb_sync).
+ * - Dense field layouts: a scalar field is [ny][nx] (x fastest); the
+ *   distributions are [16][ny][nx], plane q = the paper's velocity i = q+1.
+ */
+#ifndef MRTLB_H
+#define MRTLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRTLB_NQ 16
+
+typedef struct mrtlb_ctx mrtlb_ctx;
+
+typedef enum {
+  MRTLB_OK = 0,
+  MRTLB_ERR_ARG = -1,          /* invalid argument, size or stability limit */
+  MRTLB_ERR_UNSUPPORTED = -2,  /* velocity set or M other than the paper's */
+  MRTLB_ERR_SINGULAR = -3,     /* M not invertible */
+  MRTLB_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+  MRTLB_ERR_NONPHYSICAL = -5,  /* rho <= 0, T <= 0 or non-finite state met */
+  MRTLB_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
+  MRTLB_ERR_STATE = -7         /* call out of order (e.g. step before bind) */
+} mrtlb_status;
+
+typedef enum {
+  MRTLB_BC_PERIODIC = 0,  /* ghost = opposite edge (Sec. IV A, IV B) */
+  MRTLB_BC_OUTFLOW = 1,   /* zero-gradient extrapolation (Sec. IV B) */
+  MRTLB_BC_WALL_NEE = 2   /* non-equilibrium extrapolation wall (Sec. IV A) */
+} mrtlb_bc_kind;
+
+typedef enum { MRTLB_FP32 = 0, MRTLB_FP64 = 1 } mrtlb_precision;
+
+typedef struct {
+  int kind;        /* mrtlb_bc_kind */
+  double ux, uy;   /* wall velocity (MRTLB_BC_WALL_NEE only) */
+  double T;        /* wall temperature (MRTLB_BC_WALL_NEE only) */
+} mrtlb_bc;
+
+typedef struct {
+  int nvel;          /* number of discrete velocities; must be 16 */
+  const double* v;   /* nvel x 2 row-major (v_x, v_y): must be the D2V16 set of
+                        Fig. 1 in the order fixed by rows m2, m3 of M */
+  const double* M;   /* nvel x nvel row-major: must equal the paper's M */
+  const double* s;   /* nvel relaxation rates s_1..s_16 (Sec. II), or NULL to
+                        derive them: s5 = s6 = s_visc, s7 = s8 = Pr * s_visc,
+                        all others s_other (Pr = s7/s5 = s8/s6 follows from
+                        mu = rho T / s5, lambda = 2 rho T / s7, c_p = 2) */
+  double Pr, s_visc, s_other;
+  int eq_version;    /* equilibria of moments 12, 15, 16: 1, 2 or 3 (Sec. II) */
+  int modified;      /* 1 = the paper's modified energy-flux collision */
+  int nx, ny;        /* grid nodes along x and y */
+  double dx, dy, dt; /* node spacings and time step */
+  mrtlb_bc bc[4];    /* sides -x, +x, -y, +y; periodic sides come in pairs and
+                        walls may sit on one axis only */
+  int precision;     /* MRTLB_FP32: f stored and advanced in FP32, temperature
+                        recovered in FP64; MRTLB_FP64: everything in FP64 */
+  void* stream;      /* cudaStream_t to enqueue on; NULL = legacy default */
+} mrtlb_params;
+
+/* Validate params and build a context (host only, no device work).
+ * Rejects a velocity set or M other than the paper's with
+ * MRTLB_ERR_UNSUPPORTED; a Lax-Wendroff CFL number max|v_a| dt/d_a above 1
+ * or a relaxation s_k dt above 2 (forward-Euler limit) with MRTLB_ERR_ARG.
+ * On success *out owns the context; on failure *out is NULL. */
+int mrtlb_create(const mrtlb_params* params, mrtlb_ctx** out);
+
+/* Bytes one state buffer needs (padded device layout of 16 planes with a
+ * one-node ghost layer; its inner layout is private to the library). */
+int mrtlb_state_bytes(const mrtlb_ctx* ctx, size_t* bytes);
+
+/* Bind two caller-owned device buffers of at least mrtlb_state_bytes bytes,
+ * 256-byte aligned, used as the ping-pong pair f^n / f^{n+1}.  Allocates the
+ * context's own scratch on first use.  Ghost layers are zeroed. */
+int mrtlb_bind(mrtlb_ctx* ctx, void* f_a, void* f_b, size_t bytes);
+
+/* Set the state to the discrete equilibrium f = M^-1 f^eq(rho, u, T)
+ * (Eqs. 14a-14i and the chosen version) from FP64 fields [ny][nx] (host
+ * pointers if on_device == 0, device pointers otherwise), then make wall
+ * nodes consistent with their neighbours. */
+int mrtlb_init_equilibrium(mrtlb_ctx* ctx, const double* rho, const double* ux,
+                           const double* uy, const double* T, int on_device);
+
+/* Advance nsteps >= 0 time steps.  Each step fills the ghost layer and the
+ * wall nodes from f^n, then advances every non-wall node (Sec. II-III).
+ * Asynchronous on the context stream. */
+int mrtlb_step(mrtlb_ctx* ctx, long nsteps);
+
+/* Macroscopic fields of the current state as FP64 [ny][nx]: rho = f^_1,
+ * u = (f^_2, f^_3)/rho, T = f^_4/rho - u^2/2 (Sec. II, R = 1).  Any pointer
+ * may be NULL to skip that field.  Synchronises the stream and reports any
+ * latched device error. */
+int mrtlb_macros(mrtlb_ctx* ctx, double* rho, double* ux, double* uy,
+                 double* T, int on_device);
+
+/* Global sums in FP64 over all nodes: out[0] = sum rho, out[1] = sum j_x,
+ * out[2] = sum j_y, out[3] = sum e, out[4] = max |T - T_prev| over the nodes
+ * since the previous mrtlb_reduce call (0 on the first call).
+ * Synchronises and reports any latched device error. */
+int mrtlb_reduce(mrtlb_ctx* ctx, double out[5]);
+
+/* Copy the state out / in as dense [16][ny][nx] in the context precision
+ * (float for MRTLB_FP32, double for MRTLB_FP64).  get_f synchronises. */
+int mrtlb_get_f(mrtlb_ctx* ctx, void* f, int on_device);
+int mrtlb_set_f(mrtlb_ctx* ctx, const void* f, int on_device);
+
+/* Wait for the context's stream; report any latched device error. */
+int mrtlb_sync(mrtlb_ctx* ctx);
+
+/* Step kernel selection.  MRTLB_KERNEL_TILED is the TMA-fed row-marching
+ * kernel (one CTA per column strip and row segment, rows streamed through a
+ * shared-memory ring); MRTLB_KERNEL_PLAIN is one thread per node reading its
+ * neighbours from global memory.  Both compute the same step; AUTO (the
+ * default) takes the tiled kernel when its tensor maps could be built at
+ * bind time.  Selecting TILED when it is unavailable gives
+ * MRTLB_ERR_UNSUPPORTED. */
+#define MRTLB_KERNEL_AUTO 0
+#define MRTLB_KERNEL_PLAIN 1
+#define MRTLB_KERNEL_TILED 2
+int mrtlb_set_kernel(mrtlb_ctx* ctx, int which);
+
+/* Per-launch timing of the step kernel.  Between mrtlb_timing_begin and
+ * mrtlb_timing_end, every step-kernel launch (at most max_launches of them;
+ * later ones are not timed) is bracketed by CUDA events recorded on the
+ * context stream.  mrtlb_timing_end synchronises and returns the summed
+ * device time in milliseconds and the number of timed launches. */
+int mrtlb_timing_begin(mrtlb_ctx* ctx, int max_launches);
+int mrtlb_timing_end(mrtlb_ctx* ctx, double* kernel_ms, long* launches);
+
+/* Kernel launches one time step enqueues (boundary fills and the step). */
+int mrtlb_launches_per_step(const mrtlb_ctx* ctx);
+
+/* Number of time steps taken since the last init/set. */
+long mrtlb_step_count(const mrtlb_ctx* ctx);
+
+/* Message of the last error on ctx (never NULL; "" if none).  With
+ * ctx == NULL it returns the last error of a failed mrtlb_create. */
+const char* mrtlb_last_error(const mrtlb_ctx* ctx);
+
+/* Release the context and the scratch it owns (not the bound buffers). */
+void mrtlb_destroy(mrtlb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRTLB_H */

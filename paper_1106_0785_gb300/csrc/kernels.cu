@@ -1,0 +1,330 @@
+// kernels.cu - plain step kernel, boundary fills, layout conversion,
+// equilibrium initialisation, macroscopic fields and conservation sums.
+#include "kernels.cuh"
+
+namespace mrtlb {
+
+// ---------------------------------------------------------------------------
+// Plain step: one thread per advanced node, neighbours read straight from
+// global memory (L1/L2 serve the reuse).  Used for the FP64 path and as the
+// reference launch shape for the FP32 path.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void node_velocity(const R* __restrict__ f, long long plane, long long at,
+                                              R& ux, R& uy) {
+  R g[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) g[q] = f[q * plane + at];
+  R rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const R r = recip(rho);
+  ux = jx * r;
+  uy = jy * r;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) step_plain_kernel(const R* __restrict__ fin, R* __restrict__ fout,
+                                                         Layout L, Coef<R> c, int* err) {
+  const int i = L.i0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = L.j0 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.i1 || j >= L.j1) return;
+  const long long P = L.plane;
+  const long long at = L.node(i, j);
+  const long long E = at + 1, W = at - 1, N = at + L.pitch, S = at - L.pitch;
+
+  R f[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) f[q] = fin[q * P + at];
+  R rho, jx, jy, e;
+  conserved(f, rho, jx, jy, e);
+  const R ir = recip(rho);
+  const R ux = jx * ir, uy = jy * ir;
+  const R T = temperature(rho, jx, jy, e, ir);
+
+  R uxE, uyE, uxW, uyW, uxN, uyN, uxS, uyS;
+  node_velocity(fin, P, E, uxE, uyE);
+  node_velocity(fin, P, W, uxW, uyW);
+  node_velocity(fin, P, N, uxN, uyN);
+  node_velocity(fin, P, S, uxS, uyS);
+  const R dux_dx = (uxE - uxW) * c.inv2dx, duy_dx = (uyE - uyW) * c.inv2dx;
+  const R dux_dy = (uxN - uxS) * c.inv2dy, duy_dy = (uyN - uyS) * c.inv2dy;
+
+  R C[16];
+  collision(c, f, dux_dx, dux_dy, duy_dx, duy_dy, rho, jx, jy, e, ux, uy, T, C);
+
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const R fc = f[q];
+    R A = R(0);
+    if (vx_of(q) != 0) {
+      const R ax = R(vx_of(q)) * c.a1x, bx = R(vx_of(q) * vx_of(q)) * c.b1x;
+      const R fe = fin[q * P + E], fw = fin[q * P + W];
+      A += ax * (fe - fw) - bx * (fe - R(2) * fc + fw);
+    }
+    if (vy_of(q) != 0) {
+      const R ay = R(vy_of(q)) * c.a1y, by = R(vy_of(q) * vy_of(q)) * c.b1y;
+      const R fn = fin[q * P + N], fs = fin[q * P + S];
+      A += ay * (fn - fs) - by * (fn - R(2) * fc + fs);
+    }
+    fout[q * P + at] = fc - A - C[q];
+  }
+  if (!(rho > R(0)) || !(T > R(0))) atomicOr(err, ERRBIT_NONPHYSICAL);
+}
+
+template <typename R>
+void launch_step_plain(const R* fin, R* fout, const Layout& L, const Coef<R>& c, int* err,
+                       cudaStream_t st) {
+  const int ni = L.i1 - L.i0, nj = L.j1 - L.j0;
+  if (ni <= 0 || nj <= 0) return;
+  dim3 blk(32, 4);
+  dim3 grd((ni + 31) / 32, (nj + 3) / 4);
+  step_plain_kernel<R><<<grd, blk, 0, st>>>(fin, fout, L, c, err);
+}
+
+// ---------------------------------------------------------------------------
+// Boundaries.  Walls first (non-equilibrium extrapolation of Sec. IV A; the
+// wall node takes f^eq(rho_a, u_w, T_w) + f_a - f^eq(rho_a, u_a, T_a) from
+// its fluid neighbour a), then the ghost layer (periodic copy or
+// zero-gradient outflow; behind a wall a copy keeps the ghost finite).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void bc_walls_kernel(R* f, Layout L, Coef<double> c, Walls w) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int side = -1, i = 0, j = 0, ia = 0, ja = 0;
+  // enumerate wall nodes side by side: -x, +x (ny each), -y, +y (nx each)
+  int k = t;
+  for (int s = 0; s < 4 && side < 0; ++s) {
+    const int n = (s < 2) ? L.ny : L.nx;
+    if (L.bc[s] != BC_WALL) continue;
+    if (k < n) {
+      side = s;
+      if (s == 0) { i = 0; j = k; ia = 1; ja = k; }
+      if (s == 1) { i = L.nx - 1; j = k; ia = L.nx - 2; ja = k; }
+      if (s == 2) { i = k; j = 0; ia = k; ja = 1; }
+      if (s == 3) { i = k; j = L.ny - 1; ia = k; ja = L.ny - 2; }
+    } else {
+      k -= n;
+    }
+  }
+  if (side < 0) return;
+  const long long P = L.plane;
+  const long long a = L.node(ia, ja), at = L.node(i, j);
+  double g[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) g[q] = (double)f[q * P + a];
+  double rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const double ir = 1.0 / rho;
+  const double ux = jx * ir, uy = jy * ir;
+  const double T = temperature(rho, jx, jy, e, ir);
+  double eqa[16], eqw[16], d[16], df[16];
+  equilibrium(c, rho, jx, jy, e, ux, uy, T, eqa);
+  const double uwx = w.ux[side], uwy = w.uy[side], Tw = w.T[side];
+  const double ew = rho * (Tw + 0.5 * (uwx * uwx + uwy * uwy));
+  equilibrium(c, rho, rho * uwx, rho * uwy, ew, uwx, uwy, Tw, eqw);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) d[q] = eqw[q] - eqa[q];
+  inverse_full(c, d, df);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) f[q * P + at] = (R)(g[q] + df[q]);
+}
+
+template <typename R>
+__global__ void bc_ghost_kernel(R* f, Layout L) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  const long long P = L.plane;
+  R* fq = f + q * P;
+  if (t < L.ny) {  // x sides, row j = t
+    const int j = t;
+    const long long row = (long long)(j + 1) * L.pitch;
+    const long long first = row + L.xoff, last = row + L.xoff + L.nx - 1;
+    const bool per = (L.bc[0] == BC_PERIODIC);
+    fq[first - 1] = per ? fq[last] : fq[first];
+    fq[last + 1] = per ? fq[first] : fq[last];
+  }
+  if (t < L.nx) {  // y sides, column i = t
+    const int i = t;
+    const long long first = (long long)1 * L.pitch + L.xoff + i;
+    const long long last = (long long)L.ny * L.pitch + L.xoff + i;
+    const bool per = (L.bc[2] == BC_PERIODIC);
+    fq[first - L.pitch] = per ? fq[last] : fq[first];
+    fq[last + L.pitch] = per ? fq[first] : fq[last];
+  }
+}
+
+template <typename R>
+void launch_bc(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st) {
+  int nwall = 0;
+  for (int s = 0; s < 4; ++s)
+    if (L.bc[s] == BC_WALL) nwall += (s < 2) ? L.ny : L.nx;
+  if (nwall > 0) bc_walls_kernel<R><<<(nwall + 127) / 128, 128, 0, st>>>(f, L, c64, w);
+  const int n = (L.nx > L.ny) ? L.nx : L.ny;
+  dim3 grd((n + 255) / 256, 16);
+  bc_ghost_kernel<R><<<grd, 256, 0, st>>>(f, L);
+}
+
+// ---------------------------------------------------------------------------
+// Dense [16][ny][nx] <-> padded layout.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void pack_kernel(const R* __restrict__ dense, R* __restrict__ padded, Layout L, int to_padded) {
+  const long long n = (long long)16 * L.ny * L.nx;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.nx);
+    const long long r = t / L.nx;
+    const int j = (int)(r % L.ny);
+    const int q = (int)(r / L.ny);
+    const long long p = q * L.plane + L.node(i, j);
+    if (to_padded) padded[p] = dense[t];
+    else ((R*)dense)[t] = padded[p];
+  }
+}
+
+static int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename R>
+void launch_pack(const R* dense, R* padded, const Layout& L, cudaStream_t st) {
+  const long long n = (long long)16 * L.ny * L.nx;
+  pack_kernel<R><<<grid_for(n, 256), 256, 0, st>>>(dense, padded, L, 1);
+}
+template <typename R>
+void launch_unpack(const R* padded, R* dense, const Layout& L, cudaStream_t st) {
+  const long long n = (long long)16 * L.ny * L.nx;
+  pack_kernel<R><<<grid_for(n, 256), 256, 0, st>>>(dense, (R*)padded, L, 0);
+}
+
+// ---------------------------------------------------------------------------
+// f = M^-1 f^eq(rho, u, T), computed in FP64.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void init_eq_kernel(const double* __restrict__ rho_in, const double* __restrict__ ux_in,
+                               const double* __restrict__ uy_in, const double* __restrict__ T_in,
+                               R* __restrict__ f, Layout L, Coef<double> c) {
+  const long long n = (long long)L.ny * L.nx;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.nx), j = (int)(t / L.nx);
+    const double rho = rho_in[t], ux = ux_in[t], uy = uy_in[t], T = T_in[t];
+    const double e = rho * (T + 0.5 * (ux * ux + uy * uy));
+    double eq[16], g[16];
+    equilibrium(c, rho, rho * ux, rho * uy, e, ux, uy, T, eq);
+    inverse_full(c, eq, g);
+    const long long at = L.node(i, j);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) f[q * L.plane + at] = (R)g[q];
+  }
+}
+
+template <typename R>
+void launch_init_eq(const double* rho, const double* ux, const double* uy, const double* T, R* f,
+                    const Layout& L, const Coef<double>& c64, cudaStream_t st) {
+  const long long n = (long long)L.ny * L.nx;
+  init_eq_kernel<R><<<grid_for(n, 128), 128, 0, st>>>(rho, ux, uy, T, f, L, c64);
+}
+
+// ---------------------------------------------------------------------------
+// rho, u, T in FP64 (Sec. II, R = 1).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void macros_kernel(const R* __restrict__ f, double* rho_o, double* ux_o, double* uy_o,
+                              double* T_o, Layout L) {
+  const long long n = (long long)L.ny * L.nx;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.nx), j = (int)(t / L.nx);
+    const long long at = L.node(i, j);
+    double g[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) g[q] = (double)f[q * L.plane + at];
+    double rho, jx, jy, e;
+    conserved(g, rho, jx, jy, e);
+    const double ir = 1.0 / rho;
+    if (rho_o) rho_o[t] = rho;
+    if (ux_o) ux_o[t] = jx * ir;
+    if (uy_o) uy_o[t] = jy * ir;
+    if (T_o) T_o[t] = temperature(rho, jx, jy, e, ir);
+  }
+}
+
+template <typename R>
+void launch_macros(const R* f, double* rho, double* ux, double* uy, double* T, const Layout& L,
+                   cudaStream_t st) {
+  const long long n = (long long)L.ny * L.nx;
+  macros_kernel<R><<<grid_for(n, 128), 128, 0, st>>>(f, rho, ux, uy, T, L);
+}
+
+// ---------------------------------------------------------------------------
+// Conservation sums (FP64) and the max |T - T_prev| residual.
+// Warp shuffles, then one atomic per warp.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void reduce_kernel(const R* __restrict__ f, double* acc, double* Tprev, int have_prev,
+                              Layout L) {
+  const long long n = (long long)L.ny * L.nx;
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0, mx = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % L.nx), j = (int)(t / L.nx);
+    const long long at = L.node(i, j);
+    double g[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) g[q] = (double)f[q * L.plane + at];
+    double rho, jx, jy, e;
+    conserved(g, rho, jx, jy, e);
+    s0 += rho; s1 += jx; s2 += jy; s3 += e;
+    const double T = temperature(rho, jx, jy, e, 1.0 / rho);
+    if (have_prev) {
+      const double d = fabs(T - Tprev[t]);
+      mx = (d > mx || d != d) ? d : mx;
+    }
+    Tprev[t] = T;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+    const double m = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = (m > mx || m != m) ? m : mx;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc + 0, s0);
+    atomicAdd(acc + 1, s1);
+    atomicAdd(acc + 2, s2);
+    atomicAdd(acc + 3, s3);
+    // non-negative doubles order like their bit patterns; NaN maps above inf
+    atomicMax((unsigned long long*)(acc + 4), (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+template <typename R>
+void launch_reduce(const R* f, double* acc, double* Tprev, int have_prev, const Layout& L,
+                   cudaStream_t st) {
+  const long long n = (long long)L.ny * L.nx;
+  reduce_kernel<R><<<grid_for(n, 256), 256, 0, st>>>(f, acc, Tprev, have_prev, L);
+}
+
+#define MRTLB_INSTANTIATE(R)                                                                     \
+  template void launch_step_plain<R>(const R*, R*, const Layout&, const Coef<R>&, int*,          \
+                                     cudaStream_t);                                              \
+  template void launch_bc<R>(R*, const Layout&, const Coef<double>&, const Walls&, cudaStream_t); \
+  template void launch_pack<R>(const R*, R*, const Layout&, cudaStream_t);                       \
+  template void launch_unpack<R>(const R*, R*, const Layout&, cudaStream_t);                     \
+  template void launch_init_eq<R>(const double*, const double*, const double*, const double*,    \
+                                  R*, const Layout&, const Coef<double>&, cudaStream_t);         \
+  template void launch_macros<R>(const R*, double*, double*, double*, double*, const Layout&,    \
+                                 cudaStream_t);                                                  \
+  template void launch_reduce<R>(const R*, double*, double*, int, const Layout&, cudaStream_t);
+
+MRTLB_INSTANTIATE(float)
+MRTLB_INSTANTIATE(double)
+
+}  // namespace mrtlb

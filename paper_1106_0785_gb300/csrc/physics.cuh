@@ -1,0 +1,277 @@
+// physics.cuh - per-node arithmetic of the MRT FD-LB step (device side).
+//
+// Everything here is specialised to the paper's D2V16 velocity set (Sec. II,
+// Fig. 1) and its SO(2) moment matrix M.  M is never applied as a dense
+// 16x16 matrix: its rows are radial polynomials times angular harmonics, so
+//   * inside each of the four shells (speed 1, sqrt2, 2, 2sqrt2; four
+//     velocities each) a 4-point butterfly gives the angular harmonics
+//       axis shells:     S = sum, X = a0-a2, Y = a1-a3, Q = (a0+a2)-(a1+a3)
+//       diagonal shells: S = sum, X = (b0+b3)-(b1+b2), Y = (b0+b1)-(b2+b3),
+//                        P = (b0+b2)-(b1+b3)
+//   * each moment row is a fixed radial combination of one harmonic family
+//     over the shells (S: rows 1,4,11,12; X: 2,7,9,15; Y: 3,8,10,16;
+//     Q: 5,13; P: 6,14 - the paper's 1-based numbering).
+// M^-1 factors the same way: the host inverts each family's small radial
+// matrix exactly (rational arithmetic) and passes the columns here.
+//
+// Indices are 0-based: plane q = paper velocity i = q+1, moment k = paper
+// moment k+1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mrtlb {
+
+// D2V16 (Fig. 1): order fixed by rows m2 = v_x and m3 = v_y of M.
+__host__ __device__ constexpr int vx_of(int q) {
+  return (q == 0) ? 1 : (q == 2) ? -1 : (q == 4) ? 1 : (q == 5) ? -1 : (q == 6) ? -1 : (q == 7) ? 1
+       : (q == 8) ? 2 : (q == 10) ? -2 : (q == 12) ? 2 : (q == 13) ? -2 : (q == 14) ? -2 : (q == 15) ? 2 : 0;
+}
+__host__ __device__ constexpr int vy_of(int q) {
+  return (q == 1) ? 1 : (q == 3) ? -1 : (q == 4) ? 1 : (q == 5) ? 1 : (q == 6) ? -1 : (q == 7) ? -1
+       : (q == 9) ? 2 : (q == 11) ? -2 : (q == 12) ? 2 : (q == 13) ? 2 : (q == 14) ? -2 : (q == 15) ? -2 : 0;
+}
+
+// Per-context constants.  The family inverse columns are pre-scaled by the
+// inverse-butterfly factors (1/4 for S and Q and 1/2 for X and Y on axis
+// shells, 1/4 for everything on diagonal shells).
+template <typename R>
+struct Coef {
+  // Lax-Wendroff (Sec. III): for unit speed along x, a1x = dt/(2dx),
+  // b1x = (dt/dx)^2/2; speed-2 velocities use 2*a1x and 4*b1x.
+  R a1x, b1x, a1y, b1y;
+  R inv2dx, inv2dy;   // 1/(2 dx), 1/(2 dy) for the velocity gradients
+  R rate[16];         // dt * s_k (k >= 4 used)
+  R mod[4];           // dt*(s7/s5-1), dt*(s7/s6-1), dt*(s8/s6-1), dt*(s8/s5-1)
+  R invS[4][4];       // [shell A,B,C,D][family row: k=0,3,10,11]
+  R invX[4][4];       // rows k = 1,6,8,14
+  R invY[4][4];       // rows k = 2,7,9,15
+  R invQ[2][2];       // [shell A,C][rows k = 4,12]
+  R invP[2][2];       // [shell B,D][rows k = 5,13]
+  int version;        // equilibrium version for k = 11, 14, 15
+  int modified;       // 1 = energy-flux modification on
+};
+
+template <typename R>
+struct Harm {
+  R S[4], X[4], Y[4], Q[2], P[2];  // Q: shells A,C; P: shells B,D
+};
+
+#define MRTLB_HD __host__ __device__ __forceinline__
+
+template <typename R>
+MRTLB_HD void harmonics(const R f[16], Harm<R>& h) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const R a0 = f[4 * s + 0], a1 = f[4 * s + 1], a2 = f[4 * s + 2], a3 = f[4 * s + 3];
+    const R p02 = a0 + a2, p13 = a1 + a3;
+    h.S[s] = p02 + p13;
+    if (s == 0 || s == 2) {  // axis shell
+      h.X[s] = a0 - a2;
+      h.Y[s] = a1 - a3;
+      h.Q[s >> 1] = p02 - p13;
+    } else {                 // diagonal shell
+      const R p03 = a0 + a3, p12 = a1 + a2;
+      h.X[s] = p03 - p12;
+      h.Y[s] = (a0 + a1) - (a2 + a3);
+      h.P[s >> 1] = p02 - p13;
+    }
+  }
+}
+
+// Moments of one family row from the harmonics (rows of M, Sec. II).
+template <typename R>
+MRTLB_HD void moments(const Harm<R>& h, R m[16]) {
+  const R SA = h.S[0], SB = h.S[1], SC = h.S[2], SD = h.S[3];
+  const R XA = h.X[0], XB = h.X[1], XC = h.X[2], XD = h.X[3];
+  const R YA = h.Y[0], YB = h.Y[1], YC = h.Y[2], YD = h.Y[3];
+  m[0] = (SA + SB) + (SC + SD);
+  m[3] = R(0.5) * SA + SB + R(2) * SC + R(4) * SD;
+  m[10] = R(0.25) * SA + SB + R(4) * SC + R(16) * SD;
+  m[11] = SA - R(4) * SB + R(16) * SC - R(64) * SD;
+  m[1] = (XA + XB) + R(2) * (XC + XD);
+  m[6] = R(0.5) * XA + XB + R(4) * XC + R(8) * XD;
+  m[8] = XA - R(2) * XB + R(8) * XC - R(16) * XD;
+  m[14] = XA - R(4) * XB + R(32) * XC - R(128) * XD;
+  m[2] = (YA + YB) + R(2) * (YC + YD);
+  m[7] = R(0.5) * YA + YB + R(4) * YC + R(8) * YD;
+  m[9] = -YA + R(2) * YB - R(8) * YC + R(16) * YD;
+  m[15] = -YA + R(4) * YB - R(32) * YC + R(128) * YD;
+  m[4] = h.Q[0] + R(4) * h.Q[1];
+  m[12] = h.Q[0] + R(16) * h.Q[1];
+  m[5] = h.P[0] + R(4) * h.P[1];
+  m[13] = R(2) * h.P[0] + R(32) * h.P[1];
+}
+
+// Conserved moments only: rho, j_x, j_y, e (rows 1-4 of M).
+template <typename R>
+MRTLB_HD void conserved(const R f[16], R& rho, R& jx, R& jy, R& e) {
+  Harm<R> h;
+  harmonics(f, h);
+  rho = (h.S[0] + h.S[1]) + (h.S[2] + h.S[3]);
+  e = R(0.5) * h.S[0] + h.S[1] + R(2) * h.S[2] + R(4) * h.S[3];
+  jx = (h.X[0] + h.X[1]) + R(2) * (h.X[2] + h.X[3]);
+  jy = (h.Y[0] + h.Y[1]) + R(2) * (h.Y[2] + h.Y[3]);
+}
+
+// Temperature from the conserved moments (Sec. II with R = 1):
+// T = (e rho - |j|^2 / 2) / rho^2.  The numerator, where the kinetic part
+// cancels against e behind strong shocks, is formed in FP64 from the exact
+// FP64 products of the FP32 moments; only the final scaling is FP32.
+__device__ __forceinline__ float temperature(float rho, float jx, float jy, float e, float inv_rho) {
+  const double j2 = fma((double)jy, (double)jy, (double)jx * (double)jx);
+  const double num = fma((double)e, (double)rho, -0.5 * j2);
+  return (float)num * (inv_rho * inv_rho);
+}
+__device__ __forceinline__ double temperature(double rho, double jx, double jy, double e, double inv_rho) {
+  const double j2 = fma(jy, jy, jx * jx);
+  return fma(e, rho, -0.5 * j2) * (inv_rho * inv_rho);
+}
+
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float expr(float x) { return expf(x); }
+__device__ __forceinline__ double expr(double x) { return exp(x); }
+
+// Equilibrium moments k = 4..15 (Eqs. 14a-14i and the version rule for
+// k = 11, 14, 15), given the conserved moments and u, T.
+template <typename R>
+__device__ __forceinline__ void equilibrium(const Coef<R>& c, R rho, R jx, R jy, R e,
+                                            R ux, R uy, R T, R eq[16]) {
+  const R ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
+  const R p = rho * T;
+  eq[0] = rho; eq[1] = jx; eq[2] = jy; eq[3] = e;
+  eq[4] = jx * ux - jy * uy;                      // 14a (jx^2 - jy^2)/rho
+  eq[5] = jx * uy;                                // 14b jx jy / rho
+  eq[6] = (e + p) * ux;                           // 14c
+  eq[7] = (e + p) * uy;                           // 14d
+  eq[8] = jx * (ux2 - R(3) * uy2);                // 14e
+  eq[9] = jy * (R(3) * ux2 - uy2);                // 14f
+  eq[10] = R(2) * e * e * recip(rho) - R(0.25) * rho * u2 * u2;  // 14g
+  const R w = R(6) * e - R(2) * rho * u2;
+  eq[12] = w * (ux2 - uy2);                       // 14h
+  eq[13] = w * ux * uy;                           // 14i
+  if (c.version == 2) {
+    eq[11] = R(0);
+    eq[14] = rho * ux * (R(-4) + R(10) * T + R(5) * ux2 - R(5) * uy2);
+    eq[15] = rho * uy * (R(4) - R(10) * T + R(5) * ux2 - R(5) * uy2);
+  } else if (c.version == 3) {
+    // rows 12, 15, 16 of M applied to rho/(2 pi T) exp(-(v - u)^2 / 2T)
+    R fm[16];
+    const R pre = rho * recip(R(6.283185307179586476925286766559) * T);
+    const R m2T = R(-0.5) * recip(T);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const R dx = R(vx_of(q)) - ux, dy = R(vy_of(q)) - uy;
+      fm[q] = pre * expr(m2T * (dx * dx + dy * dy));
+    }
+    Harm<R> h;
+    harmonics(fm, h);
+    eq[11] = h.S[0] - R(4) * h.S[1] + R(16) * h.S[2] - R(64) * h.S[3];
+    eq[14] = h.X[0] - R(4) * h.X[1] + R(32) * h.X[2] - R(128) * h.X[3];
+    eq[15] = -h.Y[0] + R(4) * h.Y[1] - R(32) * h.Y[2] + R(128) * h.Y[3];
+  } else {
+    eq[11] = R(0); eq[14] = R(0); eq[15] = R(0);
+  }
+}
+
+// f = M^-1 m for a full moment vector (used for equilibria and walls).
+template <typename R>
+MRTLB_HD void inverse_full(const Coef<R>& c, const R m[16], R f[16]) {
+  R S[4], X[4], Y[4], Q[2], P[2];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    S[s] = c.invS[s][0] * m[0] + c.invS[s][1] * m[3] + c.invS[s][2] * m[10] + c.invS[s][3] * m[11];
+    X[s] = c.invX[s][0] * m[1] + c.invX[s][1] * m[6] + c.invX[s][2] * m[8] + c.invX[s][3] * m[14];
+    Y[s] = c.invY[s][0] * m[2] + c.invY[s][1] * m[7] + c.invY[s][2] * m[9] + c.invY[s][3] * m[15];
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    Q[s] = c.invQ[s][0] * m[4] + c.invQ[s][1] * m[12];
+    P[s] = c.invP[s][0] * m[5] + c.invP[s][1] * m[13];
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const bool axis = (s == 0 || s == 2);
+    const R q_or_p = axis ? Q[s >> 1] : P[s >> 1];
+    if (axis) {
+      const R sp = S[s] + q_or_p, sm = S[s] - q_or_p;
+      f[4 * s + 0] = sp + X[s];
+      f[4 * s + 2] = sp - X[s];
+      f[4 * s + 1] = sm + Y[s];
+      f[4 * s + 3] = sm - Y[s];
+    } else {
+      const R spp = S[s] + q_or_p, smp = S[s] - q_or_p;
+      f[4 * s + 0] = spp + (X[s] + Y[s]);
+      f[4 * s + 2] = spp - (X[s] + Y[s]);
+      f[4 * s + 1] = smp - (X[s] - Y[s]);
+      f[4 * s + 3] = smp + (X[s] - Y[s]);
+    }
+  }
+}
+
+// f = M^-1 m for a moment vector whose conserved part m_0..m_3 is zero
+// (the collision): the conserved columns of M^-1 are skipped.
+template <typename R>
+MRTLB_HD void inverse_nonconserved(const Coef<R>& c, const R m[16], R f[16]) {
+  R S[4], X[4], Y[4], Q[2], P[2];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    S[s] = c.invS[s][2] * m[10] + c.invS[s][3] * m[11];
+    X[s] = c.invX[s][1] * m[6] + c.invX[s][2] * m[8] + c.invX[s][3] * m[14];
+    Y[s] = c.invY[s][1] * m[7] + c.invY[s][2] * m[9] + c.invY[s][3] * m[15];
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    Q[s] = c.invQ[s][0] * m[4] + c.invQ[s][1] * m[12];
+    P[s] = c.invP[s][0] * m[5] + c.invP[s][1] * m[13];
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s == 0 || s == 2) {
+      const R sp = S[s] + Q[s >> 1], sm = S[s] - Q[s >> 1];
+      f[4 * s + 0] = sp + X[s];
+      f[4 * s + 2] = sp - X[s];
+      f[4 * s + 1] = sm + Y[s];
+      f[4 * s + 3] = sm - Y[s];
+    } else {
+      const R spp = S[s] + P[s >> 1], smp = S[s] - P[s >> 1];
+      f[4 * s + 0] = spp + (X[s] + Y[s]);
+      f[4 * s + 2] = spp - (X[s] + Y[s]);
+      f[4 * s + 1] = smp - (X[s] - Y[s]);
+      f[4 * s + 3] = smp + (X[s] - Y[s]);
+    }
+  }
+}
+
+// dt * C = dt * M^-1 c with c_k = s_k (f^_k - f^eq_k) for k >= 4 (the
+// conserved components vanish) and the modification of Sec. II added to
+// k = 6, 7 (the paper's 7 and 8).  grad = (dux/dx, dux/dy, duy/dx, duy/dy).
+// Also returns rho and T through the out-parameters for error checks.
+template <typename R>
+__device__ __forceinline__ void collision(const Coef<R>& c, const R f[16], R dux_dx, R dux_dy,
+                                          R duy_dx, R duy_dy, R rho, R jx, R jy, R e,
+                                          R ux, R uy, R T, R C[16]) {
+  Harm<R> h;
+  harmonics(f, h);
+  R m[16];
+  moments(h, m);
+  R eq[16];
+  equilibrium(c, rho, jx, jy, e, ux, uy, T, eq);
+  R cc[16];
+#pragma unroll
+  for (int k = 4; k < 16; ++k) cc[k] = c.rate[k] * (m[k] - eq[k]);
+  if (c.modified) {
+    const R p = rho * T;
+    const R shear = dux_dx - duy_dy;
+    const R strain = duy_dx + dux_dy;
+    const R pux = p * ux, puy = p * uy;
+    cc[6] += c.mod[0] * pux * shear + c.mod[1] * puy * strain;
+    cc[7] += c.mod[2] * pux * strain + c.mod[3] * puy * shear;
+  }
+  cc[0] = cc[1] = cc[2] = cc[3] = R(0);
+  inverse_nonconserved(c, cc, C);
+}
+
+}  // namespace mrtlb

@@ -1,0 +1,107 @@
+"""PyTorch-facing wrapper over one mrtlb context.
+
+PyTorch owns the two device state buffers and provides the stream; the
+library's kernels do all of the work.  Host arrays are numpy float64
+[ny][nx] fields (or [16][ny][nx] for f); device arrays are contiguous CUDA
+tensors of the same shapes.
+"""
+import numpy as np
+
+from . import mrtlb as M
+
+
+class Simulation:
+    def __init__(self, cfg, device="cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.cfg = cfg
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.params = cfg.to_params(self.stream.cuda_stream)
+        self.ctx = M.mrtlb_create(self.params)
+        self.state_bytes = M.mrtlb_state_bytes(self.ctx)
+        # the caching allocator returns 512-byte aligned blocks
+        self.buffers = [torch.empty(self.state_bytes, dtype=torch.uint8, device=self.device)
+                        for _ in range(2)]
+        M.mrtlb_bind(self.ctx, self.buffers[0], self.buffers[1], self.state_bytes)
+        self.fdtype = np.float64 if cfg.precision == "fp64" else np.float32
+        self.tdtype = torch.float64 if cfg.precision == "fp64" else torch.float32
+
+    # -- state ---------------------------------------------------------------
+    def _is_dev(self, a):
+        return not isinstance(a, np.ndarray)
+
+    def init_equilibrium(self, rho, ux, uy, T):
+        arrs = [rho, ux, uy, T]
+        on_dev = self._is_dev(rho)
+        if on_dev:
+            arrs = [a.contiguous().to(self.torch.float64) for a in arrs]
+        else:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in arrs]
+        for a in arrs:
+            assert tuple(a.shape) == (self.cfg.ny, self.cfg.nx)
+        M.mrtlb_init_equilibrium(self.ctx, *arrs, on_dev)
+        self._keep = arrs
+
+    def set_f(self, f):
+        on_dev = self._is_dev(f)
+        if on_dev:
+            f = f.contiguous().to(self.tdtype)
+        else:
+            f = np.ascontiguousarray(f, dtype=self.fdtype)
+        assert tuple(f.shape) == (16, self.cfg.ny, self.cfg.nx)
+        M.mrtlb_set_f(self.ctx, f, on_dev)
+        self._keep = f
+
+    def get_f(self, on_device=False):
+        shape = (16, self.cfg.ny, self.cfg.nx)
+        if on_device:
+            out = self.torch.empty(shape, dtype=self.tdtype, device=self.device)
+        else:
+            out = np.empty(shape, dtype=self.fdtype)
+        M.mrtlb_get_f(self.ctx, out, on_device)
+        return out
+
+    def macros(self, on_device=False):
+        shape = (self.cfg.ny, self.cfg.nx)
+        if on_device:
+            outs = [self.torch.empty(shape, dtype=self.torch.float64, device=self.device)
+                    for _ in range(4)]
+        else:
+            outs = [np.empty(shape, dtype=np.float64) for _ in range(4)]
+        M.mrtlb_macros(self.ctx, *outs, on_device)
+        return tuple(outs)
+
+    def step(self, n=1):
+        M.mrtlb_step(self.ctx, n)
+
+    def reduce(self):
+        return M.mrtlb_reduce(self.ctx)
+
+    def sync(self):
+        M.mrtlb_sync(self.ctx)
+
+    def set_kernel(self, which):
+        M.mrtlb_set_kernel(self.ctx, which)
+
+    @property
+    def steps(self):
+        return M.mrtlb_step_count(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            M.mrtlb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,149 @@
+"""Seeded synthetic inputs for the paper's three workloads (Sec. IV).
+
+This module builds problem descriptions and initial macroscopic fields only;
+it holds none of the lattice Boltzmann arithmetic, so both the CUDA path and
+the CPU oracle start from the same numbers and each side forms its own
+equilibrium distributions.  Node coordinates are cell centres,
+x_i = (i + 1/2) dx, y_j = (j + 1/2) dy, except the Couette channel whose wall
+nodes sit on y = 0 and y = 1 (y_j = j dy, dy = 1/(ny - 1)).
+
+Relaxation rates per workload (Pr = s7/s5 = s8/s6):
+  Sod        s5..s8 = 1.5e4 (the paper's Riemann viscosity), others 1e5
+  Couette    s5 = s6 = 1e2, s7 = s8 = Pr * 1e2, others 1e3
+  RM         s5..s8 = 1e4 (the paper's Fig. 7(b) pair), others 1e5
+Initial jumps are tanh-smoothed (over 2 cells for Sod and the shock, 3 cells
+for the material interface): the central scheme rings a sharp jump into
+negative temperatures.
+"""
+import math
+
+import numpy as np
+
+from .mrtlb import Config
+
+GAMMA = 2.0  # 2D monatomic gas with R = 1: c_v = 1, c_p = 2
+
+
+def rates(s_visc, s_cond, s_other):
+    s = np.full(16, float(s_other))
+    s[:4] = 0.0
+    s[4] = s[5] = float(s_visc)
+    s[6] = s[7] = float(s_cond)
+    return tuple(s)
+
+
+def _smooth_step(x, x0, width):
+    return 0.5 * (1.0 + np.tanh((x - x0) / width))
+
+
+# ---------------------------------------------------------------------------
+# Sod shock tube (Sod-type Riemann problem on a thin periodic strip)
+# ---------------------------------------------------------------------------
+def sod(nx=400, ny=4, precision="fp64", dt=1e-5, left=(1.0, 1.0), right=(0.125, 0.8),
+        s_visc=1.5e4, s_cond=1.5e4, s_other=1e5, modified=True):
+    """left/right = (rho, T) with u = 0; jump at x = 0.5."""
+    dx = 1.0 / nx
+    cfg = Config(nx=nx, ny=ny, dx=dx, dy=dx, dt=dt, s=rates(s_visc, s_cond, s_other),
+                 bc=(("outflow", 0, 0, 1),) * 2 + (("periodic", 0, 0, 1),) * 2,
+                 modified=modified, precision=precision)
+    x = (np.arange(nx) + 0.5) * dx
+    w = _smooth_step(x, 0.5, 2.0 * dx)
+    rho = left[0] + (right[0] - left[0]) * w
+    T = left[1] + (right[1] - left[1]) * w
+    f = lambda a: np.ascontiguousarray(np.broadcast_to(a[None, :], (ny, nx)))
+    zero = np.zeros((ny, nx))
+    return cfg, (f(rho), zero.copy(), zero.copy(), f(T))
+
+
+# ---------------------------------------------------------------------------
+# Thermal Couette flow between NEE walls normal to y
+# ---------------------------------------------------------------------------
+def couette(Pr=1.0, nx=4, ny=200, precision="fp64", dt=1e-4, U=0.8, T0=1.0, T1=1.0,
+            s_visc=1e2, s_other=1e3, modified=True):
+    dy = 1.0 / (ny - 1)
+    cfg = Config(nx=nx, ny=ny, dx=dy, dy=dy, dt=dt, s=rates(s_visc, Pr * s_visc, s_other),
+                 bc=(("periodic", 0, 0, 1), ("periodic", 0, 0, 1),
+                     ("wall", 0.0, 0.0, T0), ("wall", U, 0.0, T1)),
+                 modified=modified, precision=precision)
+    ones = np.ones((ny, nx))
+    T = T0 + (T1 - T0) * (np.arange(ny) * dy)[:, None] * ones
+    return cfg, (ones.copy(), np.zeros((ny, nx)), np.zeros((ny, nx)), T)
+
+
+# ---------------------------------------------------------------------------
+# Richtmyer-Meshkov: Mach-1.5 shock onto a perturbed light/heavy interface
+# ---------------------------------------------------------------------------
+def normal_shock(rho1, p1, mach, g=GAMMA):
+    """Post-shock (rho2, u2, p2) and shock speed for a shock moving +x into
+    gas at rest: the textbook normal-shock (Rankine-Hugoniot) relations."""
+    m2 = mach * mach
+    rho2 = rho1 * (g + 1.0) * m2 / ((g - 1.0) * m2 + 2.0)
+    p2 = p1 * (2.0 * g * m2 - (g - 1.0)) / (g + 1.0)
+    D = mach * math.sqrt(g * p1 / rho1)
+    u2 = D * (1.0 - rho1 / rho2)
+    return rho2, u2, p2, D
+
+
+def richtmyer_meshkov(nx=4096, ny=1024, precision="fp32", dt=1e-5, mach=1.5,
+                      rho_light=1.0, rho_heavy=3.0, amp=0.02, x_iface=0.5, x_shock=0.4,
+                      s_visc=1e4, s_cond=1e4, s_other=1e5, modified=True, amplitudes=None):
+    """Light gas (rho 1) | heavy gas (rho 3), both at p = 1; interface
+    x_I(y) = x_iface + sum_k a_k cos(2 pi k y / Ly) (default a_1 = amp)."""
+    dx = 1.0 / nx
+    Ly = ny * dx
+    cfg = Config(nx=nx, ny=ny, dx=dx, dy=dx, dt=dt, s=rates(s_visc, s_cond, s_other),
+                 bc=(("outflow", 0, 0, 1),) * 2 + (("periodic", 0, 0, 1),) * 2,
+                 modified=modified, precision=precision)
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dx
+    if amplitudes is None:
+        amplitudes = [amp]
+    xi = np.full(ny, x_iface)
+    for k, a in enumerate(amplitudes, start=1):
+        xi = xi + a * np.cos(2.0 * math.pi * k * y / Ly)
+    w = _smooth_step(x[None, :], xi[:, None], 3.0 * dx)         # 0 light, 1 heavy
+    rho = rho_light + (rho_heavy - rho_light) * w
+    p = np.ones_like(rho)
+    rho2, u2, p2, _ = normal_shock(rho_light, 1.0, mach)
+    s = 1.0 - _smooth_step(x[None, :], x_shock, 2.0 * dx) * np.ones((ny, 1))  # 1 behind shock
+    rho = rho + (rho2 - rho_light) * s
+    p = p + (p2 - 1.0) * s
+    ux = u2 * s
+    T = p / rho
+    return cfg, (np.ascontiguousarray(rho), np.ascontiguousarray(ux), np.zeros((ny, nx)),
+                 np.ascontiguousarray(T))
+
+
+# ---------------------------------------------------------------------------
+# Random smooth fields for parity tests
+# ---------------------------------------------------------------------------
+def smooth_fields(nx, ny, seed, rho0=1.0, T0=1.0, amp=0.1, umax=0.3, modes=3):
+    """Periodic low-mode random fields (rho, ux, uy, T)."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx) / nx
+    y = np.arange(ny) / ny
+
+    def field():
+        out = np.zeros((ny, nx))
+        for _ in range(modes):
+            kx, ky = rng.integers(0, 3, size=2)
+            ph = rng.uniform(0, 2 * math.pi)
+            out += rng.uniform(-1, 1) * np.cos(2 * math.pi * (kx * x[None, :] + ky * y[:, None]) + ph)
+        return out / modes
+
+    rho = rho0 * (1.0 + amp * field())
+    ux = umax * field()
+    uy = umax * field()
+    T = T0 * (1.0 + amp * field())
+    return rho, ux, uy, T
+
+
+def noise(shape, seed, scale=1.0):
+    """Standard-normal array (e.g. a non-equilibrium perturbation of f)."""
+    return scale * np.random.default_rng(seed).standard_normal(shape)
+
+
+def random_distributions(nx, ny, seed, lo=0.02, hi=0.2):
+    """Positive random f of shape (16, ny, nx): a generic input for one step."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(16, ny, nx))

@@ -1,0 +1,217 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Tolerances (fixed by the method's requirements for this implementation):
+  FP64 path: 1e-12 of each plane's magnitude after one step from the same
+             state (the step reorders sums and contracts multiply-adds, so it
+             is not bitwise);
+  FP32 path: 1e-5 relative in rho, u (normalised by max |u|) and T after 1000
+             smooth-flow steps, 1e-4 relative L1 across shocks.
+Grid sizes span several column strips (128 nodes in FP32, 64 in FP64) and
+row segments, with ragged tails.
+"""
+import numpy as np
+import pytest
+
+from oracle import equilibrium as oeq
+from oracle import fdlb
+from paper_1106_0785_gb300 import mrtlb as M
+from paper_1106_0785_gb300 import workloads
+from paper_1106_0785_gb300.simulation import Simulation
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = {"plain": M.MRTLB_KERNEL_PLAIN, "tiled": M.MRTLB_KERNEL_TILED}
+
+
+def oracle_params(cfg):
+    sides = []
+    for kind, ux, uy, T in cfg.bc:
+        sides.append(fdlb.Side({"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW,
+                                "wall": fdlb.WALL}[kind], ux, uy, T))
+    return fdlb.Params(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt,
+                       s=np.asarray(cfg.s), sides=tuple(sides), version=cfg.eq_version,
+                       modified=cfg.modified)
+
+
+def rel_plane_err(a, b):
+    scale = np.abs(b).reshape(16, -1).max(1)
+    return (np.abs(a - b).reshape(16, -1).max(1) / scale).max()
+
+
+BCS = {
+    "periodic": (("periodic", 0, 0, 1),) * 4,
+    "outflow_x": (("outflow", 0, 0, 1),) * 2 + (("periodic", 0, 0, 1),) * 2,
+    "outflow_xy": (("outflow", 0, 0, 1),) * 4,
+    "walls_y": (("periodic", 0, 0, 1),) * 2 + (("wall", 0.1, 0.0, 1.1), ("wall", 0.5, -0.05, 0.95)),
+    "walls_x": (("wall", 0.02, 0.3, 1.0), ("wall", 0.0, -0.2, 1.2)) + (("outflow", 0, 0, 1),) * 2,
+}
+
+
+def _cfg(nx, ny, bc, precision, version=1, modified=True, dt=2e-4, d=0.01):
+    s = np.random.default_rng(5).uniform(50, 2000, 16)
+    s[:4] = 0
+    return M.Config(nx=nx, ny=ny, dx=d, dy=1.1 * d, dt=dt, s=tuple(s), bc=bc,
+                    eq_version=version, modified=modified, precision=precision)
+
+
+def _input(cfg, seed, noise=1e-3):
+    rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, seed)
+    nz = workloads.noise((16, cfg.ny, cfg.nx), seed + 1, noise)
+    return (rho, ux, uy, T), nz
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("bc", list(BCS))
+def test_fp64_one_step_parity(cuda, kernel, bc):
+    cfg = _cfg(300, 70, BCS[bc], "fp64")
+    (rho, ux, uy, T), nz = _input(cfg, 10)
+    p = oracle_params(cfg)
+    f0 = fdlb.prepare(oeq.feq(rho, ux, uy, T) + nz, p)
+    with Simulation(cfg) as sim:
+        sim.set_kernel(KERNELS[kernel])
+        sim.set_f(f0)
+        # get_f refills wall nodes (same values up to rounding)
+        assert rel_plane_err(sim.get_f(), f0) < 1e-13
+        sim.step(1)
+        g1 = sim.get_f()
+    f1 = fdlb.step(f0, p)
+    assert rel_plane_err(g1, f1) < 1e-12
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("version", [1, 2, 3])
+def test_fp64_multistep_parity(cuda, kernel, version):
+    cfg = _cfg(150, 37, BCS["walls_y"], "fp64", version=version)
+    (rho, ux, uy, T), nz = _input(cfg, 20)
+    p = oracle_params(cfg)
+    f0 = fdlb.prepare(oeq.feq(rho, ux, uy, T) + nz, p)
+    with Simulation(cfg) as sim:
+        sim.set_kernel(KERNELS[kernel])
+        sim.set_f(f0)
+        sim.step(20)
+        g = sim.get_f()
+    f = fdlb.run(f0, p, 20)
+    assert rel_plane_err(g, f) < 1e-11
+
+
+def test_fp64_init_equilibrium_matches_oracle(cuda):
+    cfg = _cfg(130, 20, BCS["periodic"], "fp64", version=3)
+    rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 30)
+    with Simulation(cfg) as sim:
+        sim.init_equilibrium(rho, ux, uy, T)
+        g = sim.get_f()
+        r, a, b, t = sim.macros()
+    f = oeq.feq(rho, ux, uy, T, 3)
+    assert rel_plane_err(g, f) < 1e-14
+    for x, y in ((r, rho), (a, ux), (b, uy), (t, T)):
+        assert np.abs(x - y).max() < 1e-13 * max(1.0, np.abs(y).max())
+
+
+def test_fp32_smooth_flow_1000_steps(cuda):
+    """FP32 storage with FP64 temperature recovery vs the FP64 oracle."""
+    cfg = _cfg(160, 44, BCS["periodic"], "fp32", dt=1e-4)
+    rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 40)
+    p = oracle_params(cfg)
+    f0 = oeq.feq(rho, ux, uy, T)
+    with Simulation(cfg) as sim:
+        sim.init_equilibrium(rho, ux, uy, T)
+        sim.step(1000)
+        r, a, b, t = sim.macros()
+    f = fdlb.run(f0, p, 1000)
+    ro, ao, bo, to = fdlb.macros(f)
+    assert np.abs(r / ro - 1).max() < 1e-5
+    assert np.abs(t / to - 1).max() < 1e-5
+    umax = max(np.abs(ao).max(), np.abs(bo).max())
+    assert np.abs(a - ao).max() < 1e-5 * umax and np.abs(b - bo).max() < 1e-5 * umax
+
+
+def test_fp32_across_shocks_l1(cuda):
+    """Richtmyer-Meshkov set-up (shock + interface) on 512 x 128, 200 steps."""
+    cfg, (rho, ux, uy, T) = workloads.richtmyer_meshkov(nx=512, ny=128, dt=1e-5)
+    p = oracle_params(cfg)
+    with Simulation(cfg) as sim:
+        sim.init_equilibrium(rho, ux, uy, T)
+        sim.step(200)
+        r, a, b, t = sim.macros()
+    f = fdlb.run(oeq.feq(rho, ux, uy, T), p, 200)
+    ro, ao, bo, to = fdlb.macros(f)
+    l1 = lambda x, y: np.abs(x - y).mean() / np.abs(y).mean()
+    assert l1(r, ro) < 1e-4 and l1(t, to) < 1e-4
+    assert np.abs(a - ao).mean() < 1e-4 * np.abs(ao).mean()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_full_size_rm_one_step_sampled(cuda, precision):
+    """4096 x 1024 Richtmyer-Meshkov in the bench's launch configuration:
+    one step checked at sampled nodes (tile edges, domain edges, random),
+    each recomputed by the oracle from its 3 x 3 neighbourhood."""
+    cfg, (rho, ux, uy, T) = workloads.richtmyer_meshkov(precision=precision)
+    nz = workloads.noise((16, cfg.ny, cfg.nx), 7, 1e-4)
+    p = oracle_params(cfg)
+    fin = oeq.feq(rho, ux, uy, T) + nz
+    if precision == "fp32":
+        fin = fin.astype(np.float32)
+    with Simulation(cfg) as sim:
+        sim.set_f(fin)
+        sim.step(1)
+        out = sim.get_f()
+    fin = fin.astype(np.float64)
+    rng = np.random.default_rng(8)
+    xs = list(rng.integers(0, cfg.nx, 1500)) + [0, 1, 2, 127, 128, 129, 2047, 2048, cfg.nx - 2, cfg.nx - 1]
+    ys = list(rng.integers(0, cfg.ny, 1500)) + [0, 1, 53, 54, 55, 511, 512, 600, cfg.ny - 2, cfg.ny - 1]
+    xs = np.array(xs)
+    ys = np.array(ys)
+    # ghost layer by the oracle's boundary rule, then 3 x 3 patches side by side
+    g = fdlb._ghosts(fin, p)
+    K = len(xs)
+    patches = np.zeros((16, 3, 3 * K))
+    for k, (x, y) in enumerate(zip(xs, ys)):
+        patches[:, :, 3 * k:3 * k + 3] = g[:, y:y + 3, x:x + 3]
+    pp = fdlb.Params(nx=3 * K, ny=3, dx=p.dx, dy=p.dy, dt=p.dt, s=p.s, modified=p.modified)
+    ref = fdlb.step(patches, pp)[:, 1, 1::3]
+    got = out[:, ys, xs].astype(np.float64)
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert (np.abs(got - ref) / scale).max() < tol
+
+
+def test_conservation_sums(cuda):
+    cfg = _cfg(257, 33, BCS["periodic"], "fp64")
+    (rho, ux, uy, T), nz = _input(cfg, 50)
+    f0 = oeq.feq(rho, ux, uy, T) + nz
+    with Simulation(cfg) as sim:
+        sim.set_f(f0)
+        a = sim.reduce()
+        sim.step(10)
+        b = sim.reduce()
+    r, jx, jy, e = oeq.conserved(f0)
+    ref = np.array([r.sum(), jx.sum(), jy.sum(), e.sum()])
+    assert np.allclose(a[:4], ref, rtol=1e-13, atol=1e-12 * np.abs(ref).max())
+    assert np.allclose(b[:4], a[:4], rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    assert a[4] == 0.0 and b[4] > 0.0
+
+
+def test_nonphysical_state_is_reported(cuda):
+    cfg = _cfg(64, 8, BCS["periodic"], "fp32")
+    rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 60)
+    T[3, 5] = -0.5  # a negative temperature in the input
+    with Simulation(cfg) as sim:
+        sim.init_equilibrium(rho, ux, uy, T)
+        sim.step(1)
+        with pytest.raises(M.MrtlbError) as ei:
+            sim.sync()
+        assert ei.value.code == M.MRTLB_ERR_NONPHYSICAL
+
+
+def test_tiled_and_plain_agree_fp32(cuda):
+    cfg = _cfg(300, 70, BCS["walls_y"], "fp32")
+    (rho, ux, uy, T), nz = _input(cfg, 70)
+    res = []
+    for k in ("plain", "tiled"):
+        with Simulation(cfg) as sim:
+            sim.set_kernel(KERNELS[k])
+            sim.init_equilibrium(rho, ux, uy, T)
+            sim.step(50)
+            res.append(sim.get_f())
+    # two FP32 roundings of the same arithmetic, 50 steps apart from FMA contraction
+    assert rel_plane_err(res[1], res[0]) < 1e-5
