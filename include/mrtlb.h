@@ -160,6 +160,33 @@ int mrtlb_timing_end(mrtlb_ctx* ctx, double* kernel_ms, long* launches);
 /* Kernel launches one time step enqueues (boundary fills and the step). */
 int mrtlb_launches_per_step(const mrtlb_ctx* ctx);
 
+/* Allocation-free conservation sums.  The paper has no counterpart: this is
+ * a library convenience for callers that cannot call cudaMalloc, e.g. code
+ * whose device memory belongs to another allocator with a fixed budget, or a
+ * loop that must not pay cudaMalloc's implicit device-wide synchronisation.
+ *
+ * f: device pointer to a dense state [16][ny][nx] (float for MRTLB_FP32,
+ * double for MRTLB_FP64), e.g. filled by mrtlb_get_f(ctx, f, 1).  Computes
+ * the same out[0..4] as mrtlb_reduce: FP64 sums of rho, j_x, j_y, e and
+ * max |T - T_prev|, where T_prev are the temperatures this function stored
+ * on the same device at its previous call if that call had the same nx and
+ * ny (out[4] = 0 otherwise).  stream: cudaStream_t (NULL = legacy default);
+ * the call synchronises it.
+ *
+ * Scratch lives in one file-scope static device array of
+ * MRTLB_NOALLOC_MAX_NODES + 8 doubles (8 MiB), which every GPU that loads
+ * this library holds until the process exits.  nx * ny above
+ * MRTLB_NOALLOC_MAX_NODES is rejected with MRTLB_ERR_ARG before any device
+ * work.  The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The call allocates nothing.  All calls on a
+ * device share the array (accumulators are cleared at each call, T_prev is
+ * kept): calls that overlap on the GPU race.  CUDA failures give
+ * MRTLB_ERR_CUDA. */
+#define MRTLB_NOALLOC_MAX_NODES (1 << 20)
+int mrtlb_reduce_noalloc(const void* f, int nx, int ny, int precision, void* stream,
+                         double out[5]);
+
 /* Number of time steps taken since the last init/set. */
 long mrtlb_step_count(const mrtlb_ctx* ctx);
 

@@ -41,7 +41,10 @@ EXPORTS = (
     "mrtlb_step", "mrtlb_macros", "mrtlb_reduce", "mrtlb_get_f", "mrtlb_set_f",
     "mrtlb_sync", "mrtlb_set_kernel", "mrtlb_step_count", "mrtlb_last_error",
     "mrtlb_destroy", "mrtlb_timing_begin", "mrtlb_timing_end", "mrtlb_launches_per_step",
+    "mrtlb_reduce_noalloc",
 )
+
+MRTLB_NOALLOC_MAX_NODES = 1 << 20
 
 
 class MrtlbError(RuntimeError):
@@ -105,6 +108,8 @@ def load(path=LIB_PATH):
     lib.mrtlb_timing_begin.argtypes = [P, ctypes.c_int]
     lib.mrtlb_timing_end.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]
     lib.mrtlb_launches_per_step.argtypes = [P]
+    lib.mrtlb_reduce_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                         ctypes.POINTER(ctypes.c_double)]
     _lib = lib
     return lib
 
@@ -203,6 +208,21 @@ def mrtlb_timing_end(ctx):
     n = ctypes.c_long()
     _check(load().mrtlb_timing_end(ctx, ctypes.byref(ms), ctypes.byref(n)), ctx)
     return ms.value, n.value
+
+
+def mrtlb_reduce_noalloc(f, nx, ny, precision, stream=None):
+    """Allocation-free conservation sums of a dense device state
+    [16][ny][nx] (see include/mrtlb.h); returns out[0..4]."""
+    if nx * ny > MRTLB_NOALLOC_MAX_NODES:
+        raise MrtlbError(MRTLB_ERR_ARG, "mrtlb_reduce_noalloc: %d x %d = %d nodes exceeds its static "
+                         "scratch of %d nodes" % (nx, ny, nx * ny, MRTLB_NOALLOC_MAX_NODES))
+    out = (ctypes.c_double * 5)()
+    code = load().mrtlb_reduce_noalloc(_ptr(f), int(nx), int(ny), int(precision), stream, out)
+    if code != MRTLB_OK:
+        raise MrtlbError(code, "mrtlb_reduce_noalloc failed (%s)" % (
+            "bad argument or size above the static scratch limit" if code == MRTLB_ERR_ARG
+            else "CUDA error"))
+    return np.array(out[:], dtype=np.float64)
 
 
 def mrtlb_launches_per_step(ctx):
