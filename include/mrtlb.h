@@ -111,9 +111,12 @@ int mrtlb_bind(mrtlb_ctx* ctx, void* f_a, void* f_b, size_t bytes);
 int mrtlb_init_equilibrium(mrtlb_ctx* ctx, const double* rho, const double* ux,
                            const double* uy, const double* T, int on_device);
 
-/* Advance nsteps >= 0 time steps.  Each step fills the ghost layer and the
- * wall nodes from f^n, then advances every non-wall node (Sec. II-III).
- * Asynchronous on the context stream. */
+/* Advance nsteps >= 0 time steps.  Each step refills the wall nodes from
+ * f^n (when there are walls), then advances every non-wall node
+ * (Sec. II-III); the step kernel also writes the new values of edge nodes
+ * into the ghost layer of f^{n+1} that mirrors them (periodic or outflow),
+ * so a step costs one kernel launch, two with walls.  Asynchronous on the
+ * context stream. */
 int mrtlb_step(mrtlb_ctx* ctx, long nsteps);
 
 /* Macroscopic fields of the current state as FP64 [ny][nx]: rho = f^_1,

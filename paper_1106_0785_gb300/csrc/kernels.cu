@@ -50,24 +50,26 @@ __global__ void __launch_bounds__(128) step_plain_kernel(const R* __restrict__ f
   const R dux_dy = (uxN - uxS) * c.inv2dy, duy_dy = (uyN - uyS) * c.inv2dy;
 
   R C[16];
-  collision(c, f, dux_dx, dux_dy, duy_dx, duy_dy, rho, jx, jy, e, ux, uy, T, C);
+  collision(c, f, dux_dx, dux_dy, duy_dx, duy_dy, rho, ir, jx, jy, e, ux, uy, T, C);
 
+  R vout[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const R fc = f[q];
-    R A = R(0);
+    R fn = fc - C[q];
     if (vx_of(q) != 0) {
-      const R ax = R(vx_of(q)) * c.a1x, bx = R(vx_of(q) * vx_of(q)) * c.b1x;
-      const R fe = fin[q * P + E], fw = fin[q * P + W];
-      A += ax * (fe - fw) - bx * (fe - R(2) * fc + fw);
+      fn += c.lw[q][0] * (fin[q * P + E] - fc);
+      fn += c.lw[q][1] * (fin[q * P + W] - fc);
     }
     if (vy_of(q) != 0) {
-      const R ay = R(vy_of(q)) * c.a1y, by = R(vy_of(q) * vy_of(q)) * c.b1y;
-      const R fn = fin[q * P + N], fs = fin[q * P + S];
-      A += ay * (fn - fs) - by * (fn - R(2) * fc + fs);
+      fn += c.lw[q][2] * (fin[q * P + N] - fc);
+      fn += c.lw[q][3] * (fin[q * P + S] - fc);
     }
-    fout[q * P + at] = fc - A - C[q];
+    fout[q * P + at] = fn;
+    vout[q] = fn;
   }
+  const GhostTargets g = ghost_targets(L, i, j);
+  if (g.any()) write_ghosts(g, P, vout, fout + at);
   if (!(rho > R(0)) || !(T > R(0))) atomicOr(err, ERRBIT_NONPHYSICAL);
 }
 
@@ -118,10 +120,10 @@ __global__ void bc_walls_kernel(R* f, Layout L, Coef<double> c, Walls w) {
   const double ux = jx * ir, uy = jy * ir;
   const double T = temperature(rho, jx, jy, e, ir);
   double eqa[16], eqw[16], d[16], df[16];
-  equilibrium(c, rho, jx, jy, e, ux, uy, T, eqa);
+  equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eqa);
   const double uwx = w.ux[side], uwy = w.uy[side], Tw = w.T[side];
   const double ew = rho * (Tw + 0.5 * (uwx * uwx + uwy * uwy));
-  equilibrium(c, rho, rho * uwx, rho * uwy, ew, uwx, uwy, Tw, eqw);
+  equilibrium(c, rho, ir, rho * uwx, rho * uwy, ew, uwx, uwy, Tw, eqw);
 #pragma unroll
   for (int q = 0; q < 16; ++q) d[q] = eqw[q] - eqa[q];
   inverse_full(c, d, df);
@@ -154,11 +156,16 @@ __global__ void bc_ghost_kernel(R* f, Layout L) {
 }
 
 template <typename R>
-void launch_bc(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st) {
+void launch_walls(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st) {
   int nwall = 0;
   for (int s = 0; s < 4; ++s)
     if (L.bc[s] == BC_WALL) nwall += (s < 2) ? L.ny : L.nx;
   if (nwall > 0) bc_walls_kernel<R><<<(nwall + 127) / 128, 128, 0, st>>>(f, L, c64, w);
+}
+
+template <typename R>
+void launch_bc(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st) {
+  launch_walls<R>(f, L, c64, w, st);
   const int n = (L.nx > L.ny) ? L.nx : L.ny;
   dim3 grd((n + 255) / 256, 16);
   bc_ghost_kernel<R><<<grd, 256, 0, st>>>(f, L);
@@ -169,17 +176,15 @@ void launch_bc(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, c
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void pack_kernel(const R* __restrict__ dense, R* __restrict__ padded, Layout L, int to_padded) {
-  const long long n = (long long)16 * L.ny * L.nx;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % L.nx);
-    const long long r = t / L.nx;
-    const int j = (int)(r % L.ny);
-    const int q = (int)(r / L.ny);
-    const long long p = q * L.plane + L.node(i, j);
-    if (to_padded) padded[p] = dense[t];
-    else ((R*)dense)[t] = padded[p];
-  }
+  // grid: x over columns, y over rows, z over planes (no divisions)
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  const int q = blockIdx.z;
+  if (i >= L.nx) return;
+  const long long d = ((long long)q * L.ny + j) * L.nx + i;
+  const long long p = q * L.plane + L.node(i, j);
+  if (to_padded) padded[p] = dense[d];
+  else ((R*)dense)[d] = padded[p];
 }
 
 static int grid_for(long long n, int threads) {
@@ -191,13 +196,13 @@ static int grid_for(long long n, int threads) {
 
 template <typename R>
 void launch_pack(const R* dense, R* padded, const Layout& L, cudaStream_t st) {
-  const long long n = (long long)16 * L.ny * L.nx;
-  pack_kernel<R><<<grid_for(n, 256), 256, 0, st>>>(dense, padded, L, 1);
+  dim3 grd((L.nx + 255) / 256, L.ny, 16);
+  pack_kernel<R><<<grd, 256, 0, st>>>(dense, padded, L, 1);
 }
 template <typename R>
 void launch_unpack(const R* padded, R* dense, const Layout& L, cudaStream_t st) {
-  const long long n = (long long)16 * L.ny * L.nx;
-  pack_kernel<R><<<grid_for(n, 256), 256, 0, st>>>(dense, (R*)padded, L, 0);
+  dim3 grd((L.nx + 255) / 256, L.ny, 16);
+  pack_kernel<R><<<grd, 256, 0, st>>>(dense, (R*)padded, L, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -214,7 +219,7 @@ __global__ void init_eq_kernel(const double* __restrict__ rho_in, const double* 
     const double rho = rho_in[t], ux = ux_in[t], uy = uy_in[t], T = T_in[t];
     const double e = rho * (T + 0.5 * (ux * ux + uy * uy));
     double eq[16], g[16];
-    equilibrium(c, rho, rho * ux, rho * uy, e, ux, uy, T, eq);
+    equilibrium(c, rho, 1.0 / rho, rho * ux, rho * uy, e, ux, uy, T, eq);
     inverse_full(c, eq, g);
     const long long at = L.node(i, j);
 #pragma unroll
@@ -232,32 +237,33 @@ void launch_init_eq(const double* rho, const double* ux, const double* uy, const
 // ---------------------------------------------------------------------------
 // rho, u, T in FP64 (Sec. II, R = 1).
 // ---------------------------------------------------------------------------
+// Moment sums in the storage precision (FP32 states: the same recovery as
+// the step, FP32 sums and an FP64 temperature numerator), outputs in FP64.
 template <typename R>
 __global__ void macros_kernel(const R* __restrict__ f, double* rho_o, double* ux_o, double* uy_o,
                               double* T_o, Layout L) {
-  const long long n = (long long)L.ny * L.nx;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % L.nx), j = (int)(t / L.nx);
-    const long long at = L.node(i, j);
-    double g[16];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= L.nx) return;
+  const long long t = (long long)j * L.nx + i;
+  const long long at = L.node(i, j);
+  R g[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) g[q] = (double)f[q * L.plane + at];
-    double rho, jx, jy, e;
-    conserved(g, rho, jx, jy, e);
-    const double ir = 1.0 / rho;
-    if (rho_o) rho_o[t] = rho;
-    if (ux_o) ux_o[t] = jx * ir;
-    if (uy_o) uy_o[t] = jy * ir;
-    if (T_o) T_o[t] = temperature(rho, jx, jy, e, ir);
-  }
+  for (int q = 0; q < 16; ++q) g[q] = f[q * L.plane + at];
+  R rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const R ir = recip(rho);
+  if (rho_o) rho_o[t] = (double)rho;
+  if (ux_o) ux_o[t] = (double)(jx * ir);
+  if (uy_o) uy_o[t] = (double)(jy * ir);
+  if (T_o) T_o[t] = (double)temperature(rho, jx, jy, e, ir);
 }
 
 template <typename R>
 void launch_macros(const R* f, double* rho, double* ux, double* uy, double* T, const Layout& L,
                    cudaStream_t st) {
-  const long long n = (long long)L.ny * L.nx;
-  macros_kernel<R><<<grid_for(n, 128), 128, 0, st>>>(f, rho, ux, uy, T, L);
+  dim3 grd((L.nx + 127) / 128, L.ny);
+  macros_kernel<R><<<grd, 128, 0, st>>>(f, rho, ux, uy, T, L);
 }
 
 // ---------------------------------------------------------------------------
@@ -316,6 +322,7 @@ void launch_reduce(const R* f, double* acc, double* Tprev, int have_prev, const 
   template void launch_step_plain<R>(const R*, R*, const Layout&, const Coef<R>&, int*,          \
                                      cudaStream_t);                                              \
   template void launch_bc<R>(R*, const Layout&, const Coef<double>&, const Walls&, cudaStream_t); \
+  template void launch_walls<R>(R*, const Layout&, const Coef<double>&, const Walls&, cudaStream_t); \
   template void launch_pack<R>(const R*, R*, const Layout&, cudaStream_t);                       \
   template void launch_unpack<R>(const R*, R*, const Layout&, cudaStream_t);                     \
   template void launch_init_eq<R>(const double*, const double*, const double*, const double*,    \

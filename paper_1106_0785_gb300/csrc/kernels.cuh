@@ -33,6 +33,45 @@ struct Layout {
   }
 };
 
+// Ghost cells that mirror an advanced edge node (x, j): periodic sides
+// mirror the opposite edge, zero-gradient outflow sides their own edge.
+// A step that writes these from the new values keeps the ghost layer of
+// f^{n+1} complete, so the next step needs no separate boundary launch.
+// Walls have no ghosts in use.  Offsets are relative to node (x, j).
+struct GhostTargets {
+  bool w[4];
+  long long off[4];
+  __device__ __forceinline__ bool any() const { return w[0] || w[1] || w[2] || w[3]; }
+};
+
+__device__ __forceinline__ GhostTargets ghost_targets(const Layout& L, int x, int j) {
+  const bool xl = (x == 0), xr = (x == L.nx - 1), yl = (j == 0), yr = (j == L.ny - 1);
+  GhostTargets g;
+  // ghost column -1 mirrors column 0 (outflow) or column nx-1 (periodic), etc.
+  g.w[0] = (xl && L.bc[0] == BC_OUTFLOW) || (xr && L.bc[0] == BC_PERIODIC);
+  g.w[1] = (xr && L.bc[1] == BC_OUTFLOW) || (xl && L.bc[1] == BC_PERIODIC);
+  g.w[2] = (yl && L.bc[2] == BC_OUTFLOW) || (yr && L.bc[2] == BC_PERIODIC);
+  g.w[3] = (yr && L.bc[3] == BC_OUTFLOW) || (yl && L.bc[3] == BC_PERIODIC);
+  g.off[0] = -(long long)x - 1;
+  g.off[1] = (long long)(L.nx - x);
+  g.off[2] = -(long long)(j + 1) * L.pitch;
+  g.off[3] = (long long)(L.ny - j) * L.pitch;
+  return g;
+}
+
+// Write the 16 new values of a node (plane-0 address `out`) to its ghosts.
+template <typename R>
+__device__ __forceinline__ void write_ghosts(const GhostTargets& g, long long plane, const R v[16],
+                                             R* out) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (!g.w[s]) continue;
+    R* p = out + g.off[s];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) p[q * plane] = v[q];
+  }
+}
+
 struct Walls {
   double ux[4], uy[4], T[4];  // per side
 };
@@ -42,6 +81,9 @@ void launch_step_plain(const R* fin, R* fout, const Layout& L, const Coef<R>& c,
                        cudaStream_t st);
 template <typename R>
 void launch_bc(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st);
+// wall nodes only (the per-step fill; the step kernels keep the ghosts)
+template <typename R>
+void launch_walls(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st);
 template <typename R>
 void launch_pack(const R* dense, R* padded, const Layout& L, cudaStream_t st);
 template <typename R>

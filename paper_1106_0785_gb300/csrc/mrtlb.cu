@@ -154,6 +154,14 @@ static int build_coefficients(mrtlb_ctx* c) {
   k.b1y = 0.5 * (p.dt / p.dy) * (p.dt / p.dy);
   k.inv2dx = 1.0 / (2.0 * p.dx);
   k.inv2dy = 1.0 / (2.0 * p.dy);
+  for (int q = 0; q < 16; ++q) {
+    const double ax = vx_of(q) * k.a1x, bx = vx_of(q) * vx_of(q) * k.b1x;
+    const double ay = vy_of(q) * k.a1y, by = vy_of(q) * vy_of(q) * k.b1y;
+    k.lw[q][0] = bx - ax;  // east  (x + dx)
+    k.lw[q][1] = bx + ax;  // west  (x - dx)
+    k.lw[q][2] = by - ay;  // north (y + dy)
+    k.lw[q][3] = by + ay;  // south (y - dy)
+  }
   for (int q = 0; q < 16; ++q) k.rate[q] = (q >= 4) ? p.dt * c->s[q] : 0.0;
   if (p.modified) {
     const double s5 = c->s[4], s6 = c->s[5], s7 = c->s[6], s8 = c->s[7];
@@ -209,6 +217,8 @@ static int build_coefficients(mrtlb_ctx* c) {
   Coef<float>& f = c->c32;
   f.a1x = (float)k.a1x; f.b1x = (float)k.b1x; f.a1y = (float)k.a1y; f.b1y = (float)k.b1y;
   f.inv2dx = (float)k.inv2dx; f.inv2dy = (float)k.inv2dy;
+  for (int q = 0; q < 16; ++q)
+    for (int a = 0; a < 4; ++a) f.lw[q][a] = (float)k.lw[q][a];
   for (int q = 0; q < 16; ++q) f.rate[q] = (float)k.rate[q];
   for (int q = 0; q < 4; ++q) f.mod[q] = (float)k.mod[q];
   for (int a = 0; a < 4; ++a)
@@ -249,7 +259,8 @@ extern "C" int mrtlb_create(const mrtlb_params* params, mrtlb_ctx** out) {
       if (p.M[k * 16 + q] != m[k])
         return fail(nullptr, MRTLB_ERR_UNSUPPORTED, "M[%d][%d] = %g differs from the paper's %g", k + 1, q + 1, p.M[k * 16 + q], m[k]);
   }
-  if (p.nx < 1 || p.ny < 1) return fail(nullptr, MRTLB_ERR_ARG, "grid %d x %d", p.nx, p.ny);
+  if (p.nx < 1 || p.ny < 1 || p.ny > 65535)
+    return fail(nullptr, MRTLB_ERR_ARG, "grid %d x %d (need nx >= 1, 1 <= ny <= 65535)", p.nx, p.ny);
   if (!(p.dx > 0) || !(p.dy > 0) || !(p.dt > 0)) return fail(nullptr, MRTLB_ERR_ARG, "dx, dy, dt must be positive");
   if (p.eq_version < 1 || p.eq_version > 3) return fail(nullptr, MRTLB_ERR_ARG, "eq_version %d", p.eq_version);
   if (p.precision != MRTLB_FP32 && p.precision != MRTLB_FP64) return fail(nullptr, MRTLB_ERR_ARG, "precision %d", p.precision);
@@ -375,6 +386,11 @@ extern "C" int mrtlb_bind(mrtlb_ctx* c, void* f_a, void* f_b, size_t bytes) {
 
 static bool bound(mrtlb_ctx* c) { return c && c->f[0] && c->f[1]; }
 
+static void enqueue_walls(mrtlb_ctx* c, void* f) {
+  if (c->prec == MRTLB_FP64) launch_walls<double>((double*)f, c->L, c->c64, c->walls, c->stream);
+  else launch_walls<float>((float*)f, c->L, c->c64, c->walls, c->stream);
+}
+
 static void enqueue_bc(mrtlb_ctx* c, void* f) {
   if (c->prec == MRTLB_FP64) launch_bc<double>((double*)f, c->L, c->c64, c->walls, c->stream);
   else launch_bc<float>((float*)f, c->L, c->c64, c->walls, c->stream);
@@ -417,7 +433,7 @@ static int enqueue_steps(mrtlb_ctx* c, long nsteps) {
   for (long n = 0; n < nsteps; ++n) {
     void* fin = c->f[c->cur];
     void* fout = c->f[c->cur ^ 1];
-    enqueue_bc(c, fin);
+    enqueue_walls(c, fin);  // ghosts of fin were written through by the previous step
     const bool timed = c->timing && c->ev_used < c->ev_cap;
     if (timed) cudaEventRecord(c->ev[2 * c->ev_used], c->stream);
     if (c->prec == MRTLB_FP64) {
@@ -580,9 +596,9 @@ extern "C" int mrtlb_timing_end(mrtlb_ctx* c, double* kernel_ms, long* launches)
 
 extern "C" int mrtlb_launches_per_step(const mrtlb_ctx* c) {
   if (!c) return MRTLB_ERR_ARG;
-  int n = 2;  // ghost fill + step
+  int n = 1;  // the step (it writes the ghost layer through)
   for (int s = 0; s < 4; ++s)
-    if (c->L.bc[s] == BC_WALL) { ++n; break; }
+    if (c->L.bc[s] == BC_WALL) { ++n; break; }  // + the wall fill
   return n;
 }
 

@@ -42,6 +42,10 @@ struct Coef {
   // b1x = (dt/dx)^2/2; speed-2 velocities use 2*a1x and 4*b1x.
   R a1x, b1x, a1y, b1y;
   R inv2dx, inv2dy;   // 1/(2 dx), 1/(2 dy) for the velocity gradients
+  // the same scheme per velocity in neighbour-difference form:
+  // f_new = f + kE (f_E - f) + kW (f_W - f) + kN (f_N - f) + kS (f_S - f) - dt C,
+  // kE = b_x - a_x, kW = b_x + a_x (a_x = v_x dt/2dx, b_x = (v_x dt/dx)^2/2), same in y
+  R lw[16][4];
   R rate[16];         // dt * s_k (k >= 4 used)
   R mod[4];           // dt*(s7/s5-1), dt*(s7/s6-1), dt*(s8/s6-1), dt*(s8/s5-1)
   R invS[4][4];       // [shell A,B,C,D][family row: k=0,3,10,11]
@@ -129,7 +133,14 @@ __device__ __forceinline__ double temperature(double rho, double jx, double jy, 
   return fma(e, rho, -0.5 * j2) * (inv_rho * inv_rho);
 }
 
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// 1/x: the hardware approximation refined by one Newton-Raphson step
+// r <- r (2 - x r), which roughly squares the relative error of the
+// approximation (about 2^-22 before the step).
+__device__ __forceinline__ float recip(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r * fmaf(-x, r, 2.0f);
+}
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float expr(float x) { return expf(x); }
 __device__ __forceinline__ double expr(double x) { return exp(x); }
@@ -137,7 +148,7 @@ __device__ __forceinline__ double expr(double x) { return exp(x); }
 // Equilibrium moments k = 4..15 (Eqs. 14a-14i and the version rule for
 // k = 11, 14, 15), given the conserved moments and u, T.
 template <typename R>
-__device__ __forceinline__ void equilibrium(const Coef<R>& c, R rho, R jx, R jy, R e,
+__device__ __forceinline__ void equilibrium(const Coef<R>& c, R rho, R inv_rho, R jx, R jy, R e,
                                             R ux, R uy, R T, R eq[16]) {
   const R ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
   const R p = rho * T;
@@ -148,7 +159,7 @@ __device__ __forceinline__ void equilibrium(const Coef<R>& c, R rho, R jx, R jy,
   eq[7] = (e + p) * uy;                           // 14d
   eq[8] = jx * (ux2 - R(3) * uy2);                // 14e
   eq[9] = jy * (R(3) * ux2 - uy2);                // 14f
-  eq[10] = R(2) * e * e * recip(rho) - R(0.25) * rho * u2 * u2;  // 14g
+  eq[10] = R(2) * e * e * inv_rho - R(0.25) * rho * u2 * u2;  // 14g
   const R w = R(6) * e - R(2) * rho * u2;
   eq[12] = w * (ux2 - uy2);                       // 14h
   eq[13] = w * ux * uy;                           // 14i
@@ -251,14 +262,14 @@ MRTLB_HD void inverse_nonconserved(const Coef<R>& c, const R m[16], R f[16]) {
 // Also returns rho and T through the out-parameters for error checks.
 template <typename R>
 __device__ __forceinline__ void collision(const Coef<R>& c, const R f[16], R dux_dx, R dux_dy,
-                                          R duy_dx, R duy_dy, R rho, R jx, R jy, R e,
+                                          R duy_dx, R duy_dy, R rho, R inv_rho, R jx, R jy, R e,
                                           R ux, R uy, R T, R C[16]) {
   Harm<R> h;
   harmonics(f, h);
   R m[16];
   moments(h, m);
   R eq[16];
-  equilibrium(c, rho, jx, jy, e, ux, uy, T, eq);
+  equilibrium(c, rho, inv_rho, jx, jy, e, ux, uy, T, eq);
   R cc[16];
 #pragma unroll
   for (int k = 4; k < 16; ++k) cc[k] = c.rate[k] * (m[k] - eq[k]);
