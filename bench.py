@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -351,6 +353,11 @@ def run_mine(args, world, rank, local):
     sim64.close()
     fp64_mlups = world * nodes * args.fp64_steps / (ms64 / 1e3) / 1e6
 
+    # ---- the batched set: 64 uneven Sod-type / Couette instances -----------
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(args, world, dev)
+
     if rank != 0:
         return
     line = {
@@ -367,11 +374,63 @@ def run_mine(args, world, rank, local):
         "roofline": roofline,
         "fp64_mlups": fp64_mlups,
         "fp64_ms_per_step": ms64 / args.fp64_steps,
+        "batched": batched,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
+
+
+def run_batched(args, world, dev):
+    """64 seeded instances (grids 128-2048 x 4-256, Sod-type and Couette,
+    Pr 0.3-3) in one persistent launch per step, time loop as CUDA graphs,
+    tile shape from the autotuner (cached outside the repository)."""
+    import tempfile
+
+    import torch
+
+    from paper_1106_0785_gb300 import workloads
+    from paper_1106_0785_gb300.simulation import Batch, Simulation
+
+    insts = workloads.batched_instances(64, precision="fp32")
+    sims = []
+    for cfg, fields in insts:
+        s = Simulation(cfg, device=dev)
+        s.init_equilibrium(*fields)
+        sims.append(s)
+    b = Batch(sims)
+    cache = os.path.join(tempfile.gettempdir(), "mrtlb_batch_tune.txt")
+    b.tune(cache, trial_steps=10)
+    b.step(64)
+    b.sync()
+    stream = sims[0].stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    b.step(args.batch_steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    b.sync()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    nodes = b.nodes
+    bx, seglen, ntiles, grid = b.tiles
+    peak, _ = measured_peaks()
+    per_step_s = ms / 1e3 / args.batch_steps
+    gbs = BYTES_PER_LUP_FP32 * nodes / per_step_s / 1e9
+    out = {"instances": len(insts), "nodes": nodes, "steps": args.batch_steps,
+           "mlups": world * nodes * args.batch_steps / (ms / 1e3) / 1e6,
+           "ms_per_step": ms / args.batch_steps,
+           "step_gbs": gbs, "step_frac_of_hbm": gbs / peak,
+           "tiles": {"bx": bx, "seglen": seglen, "ntiles": ntiles, "grid": grid},
+           "launches_per_step": 2, "graph_steps": 64}
+    b.close()
+    for s in sims:
+        s.close()
+    return out
 
 
 def main():

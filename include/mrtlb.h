@@ -190,6 +190,48 @@ int mrtlb_launches_per_step(const mrtlb_ctx* ctx);
 int mrtlb_reduce_noalloc(const void* f, int nx, int ny, int precision, void* stream,
                          double out[5]);
 
+/* ------------------------------------------------------------------------
+ * Batched stepping: many independent grids (e.g. Riemann, Couette and
+ * Richtmyer-Meshkov instances of uneven sizes, rates, time steps and Mach
+ * numbers) advanced together.  The instances are contexts created and bound
+ * as usual (initialise them with mrtlb_init_equilibrium / mrtlb_set_f before
+ * mrtlb_batch_create); they must share one precision and one stream and be
+ * at the same buffer parity (no steps taken since their last init/set, or
+ * the same number).  Per time step the batch makes one launch of a
+ * persistent kernel over a tile list (instance, column strip, row segment)
+ * of all instances, plus one launch for the NEE walls of all instances that
+ * have walls; runs of graph_steps steps (default 64) replay as CUDA graphs.
+ * The instances' own calls (macros, get_f, reduce, ...) keep working on the
+ * advanced states; stepping an instance alone while it is in a batch makes
+ * the next mrtlb_batch_step return MRTLB_ERR_STATE.  The batch owns its
+ * tables and graphs, not the contexts.
+ * ---------------------------------------------------------------------- */
+typedef struct mrtlb_batch mrtlb_batch;
+
+int mrtlb_batch_create(mrtlb_ctx* const* ctxs, int n, mrtlb_batch** out);
+/* Advance every instance by nsteps time steps (asynchronous). */
+int mrtlb_batch_step(mrtlb_batch* b, long nsteps);
+/* Wait for the stream; report a latched device error of batched steps. */
+int mrtlb_batch_sync(mrtlb_batch* b);
+/* Tile shape: strip width bx (FP32: 64 or 128; FP64: 64) and rows per
+ * segment (>= 1).  The default is the single-grid shape with 32 rows. */
+int mrtlb_batch_set_tiles(mrtlb_batch* b, int bx, int seglen);
+int mrtlb_batch_get_tiles(const mrtlb_batch* b, int* bx, int* seglen, int* ntiles, int* grid);
+/* Steps per captured CUDA graph (0 = plain launches). */
+int mrtlb_batch_set_graph_steps(mrtlb_batch* b, int steps);
+/* Autotuner: time trial_steps steps for each candidate tile shape and keep
+ * the fastest; the instances' states are saved before and restored after
+ * the trials.  With cache_path, a text file of "signature bx seglen us"
+ * lines is read first (a hit skips the trials) and the result appended;
+ * the signature hashes the precision, every instance's grid and boundary
+ * kinds, and the device name. */
+int mrtlb_batch_tune(mrtlb_batch* b, const char* cache_path, int trial_steps, int* bx_out,
+                     int* seglen_out);
+/* Total nodes over all instances. */
+long long mrtlb_batch_nodes(const mrtlb_batch* b);
+const char* mrtlb_batch_last_error(const mrtlb_batch* b);
+void mrtlb_batch_destroy(mrtlb_batch* b);
+
 /* Number of time steps taken since the last init/set. */
 long mrtlb_step_count(const mrtlb_ctx* ctx);
 

@@ -1,0 +1,42 @@
+// ctx.h - the library's context (private; shared by the C ABI sources).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/mrtlb.h"
+#include "kernels.cuh"
+#include "step_tiled.cuh"
+
+using namespace mrtlb;
+
+struct mrtlb_ctx {
+  mrtlb_params p{};
+  double s[16]{};
+  int prec = MRTLB_FP32;
+  size_t esize = 4;
+  Layout L{};
+  Walls walls{};
+  Coef<double> c64{};
+  Coef<float> c32{};
+  size_t state_bytes = 0;
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  long steps = 0;
+  cudaStream_t stream = nullptr;
+  int kernel = MRTLB_KERNEL_AUTO;
+  // library-owned scratch
+  int* err = nullptr;            // device error word
+  double* acc = nullptr;         // 5 doubles for mrtlb_reduce
+  double* Tprev = nullptr;       // [ny][nx] for the residual
+  int have_prev = 0;
+  void* staging = nullptr;       // dense f or 4 FP64 fields
+  size_t staging_bytes = 0;
+  TiledPlan plan{};
+  // step-kernel timing
+  cudaEvent_t* ev = nullptr;
+  int ev_cap = 0, ev_used = 0;
+  bool timing = false;
+  std::string last_error;
+};

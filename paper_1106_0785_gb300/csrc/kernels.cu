@@ -91,44 +91,7 @@ void launch_step_plain(const R* fin, R* fout, const Layout& L, const Coef<R>& c,
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void bc_walls_kernel(R* f, Layout L, Coef<double> c, Walls w) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int side = -1, i = 0, j = 0, ia = 0, ja = 0;
-  // enumerate wall nodes side by side: -x, +x (ny each), -y, +y (nx each)
-  int k = t;
-  for (int s = 0; s < 4 && side < 0; ++s) {
-    const int n = (s < 2) ? L.ny : L.nx;
-    if (L.bc[s] != BC_WALL) continue;
-    if (k < n) {
-      side = s;
-      if (s == 0) { i = 0; j = k; ia = 1; ja = k; }
-      if (s == 1) { i = L.nx - 1; j = k; ia = L.nx - 2; ja = k; }
-      if (s == 2) { i = k; j = 0; ia = k; ja = 1; }
-      if (s == 3) { i = k; j = L.ny - 1; ia = k; ja = L.ny - 2; }
-    } else {
-      k -= n;
-    }
-  }
-  if (side < 0) return;
-  const long long P = L.plane;
-  const long long a = L.node(ia, ja), at = L.node(i, j);
-  double g[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) g[q] = (double)f[q * P + a];
-  double rho, jx, jy, e;
-  conserved(g, rho, jx, jy, e);
-  const double ir = 1.0 / rho;
-  const double ux = jx * ir, uy = jy * ir;
-  const double T = temperature(rho, jx, jy, e, ir);
-  double eqa[16], eqw[16], d[16], df[16];
-  equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eqa);
-  const double uwx = w.ux[side], uwy = w.uy[side], Tw = w.T[side];
-  const double ew = rho * (Tw + 0.5 * (uwx * uwx + uwy * uwy));
-  equilibrium(c, rho, ir, rho * uwx, rho * uwy, ew, uwx, uwy, Tw, eqw);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) d[q] = eqw[q] - eqa[q];
-  inverse_full(c, d, df);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) f[q * P + at] = (R)(g[q] + df[q]);
+  wall_node(f, L, c, w, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename R>

@@ -72,9 +72,63 @@ __device__ __forceinline__ void write_ghosts(const GhostTargets& g, long long pl
   }
 }
 
+
+
 struct Walls {
   double ux[4], uy[4], T[4];  // per side
 };
+
+// Number of wall nodes of a layout (NEE sides: ny nodes per x side, nx per y side).
+__host__ __device__ inline int wall_count(const Layout& L) {
+  int n = 0;
+  for (int s = 0; s < 4; ++s)
+    if (L.bc[s] == BC_WALL) n += (s < 2) ? L.ny : L.nx;
+  return n;
+}
+
+// Non-equilibrium extrapolation (Sec. IV A) of wall node number k (wall
+// nodes enumerated side by side: -x, +x, -y, +y): the wall node takes
+// f^eq(rho_a, u_w, T_w) + f_a - f^eq(rho_a, u_a, T_a) from its fluid
+// neighbour a, computed in FP64.
+template <typename R>
+__device__ __forceinline__ void wall_node(R* f, const Layout& L, const Coef<double>& c, const Walls& w,
+                                          int k) {
+  int side = -1, i = 0, j = 0, ia = 0, ja = 0;
+  for (int s = 0; s < 4 && side < 0; ++s) {
+    const int n = (s < 2) ? L.ny : L.nx;
+    if (L.bc[s] != BC_WALL) continue;
+    if (k < n) {
+      side = s;
+      if (s == 0) { i = 0; j = k; ia = 1; ja = k; }
+      if (s == 1) { i = L.nx - 1; j = k; ia = L.nx - 2; ja = k; }
+      if (s == 2) { i = k; j = 0; ia = k; ja = 1; }
+      if (s == 3) { i = k; j = L.ny - 1; ia = k; ja = L.ny - 2; }
+    } else {
+      k -= n;
+    }
+  }
+  if (side < 0) return;
+  const long long P = L.plane;
+  const long long a = L.node(ia, ja), at = L.node(i, j);
+  double g[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) g[q] = (double)f[q * P + a];
+  double rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const double ir = 1.0 / rho;
+  const double ux = jx * ir, uy = jy * ir;
+  const double T = temperature(rho, jx, jy, e, ir);
+  double eqa[16], eqw[16], d[16], df[16];
+  equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eqa);
+  const double uwx = w.ux[side], uwy = w.uy[side], Tw = w.T[side];
+  const double ew = rho * (Tw + 0.5 * (uwx * uwx + uwy * uwy));
+  equilibrium(c, rho, ir, rho * uwx, rho * uwy, ew, uwx, uwy, Tw, eqw);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) d[q] = eqw[q] - eqa[q];
+  inverse_full(c, d, df);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) f[q * P + at] = (R)(g[q] + df[q]);
+}
 
 template <typename R>
 void launch_step_plain(const R* fin, R* fout, const Layout& L, const Coef<R>& c, int* err,

@@ -34,6 +34,9 @@ int plan_tiled(const Layout& L, int esize, void* f0, void* f1, TiledPlan* plan);
 // Choose a segment length for a target number of CTAs.
 void plan_segments(const Layout& L, int target_ctas, TiledPlan* plan);
 bool tiled_supported(const TiledPlan& plan);
+// Row tensor maps (box = bx + 2 halo columns x 1 row x 16 planes) of two
+// state buffers; returns 0 on success.
+int encode_row_maps(const Layout& L, int esize, void* f0, void* f1, int bx, CUtensorMap out[2]);
 bool use_tiled(int which, const TiledPlan& plan, bool fp64);
 
 // Launch one step reading buffer `cur` and writing the other one.

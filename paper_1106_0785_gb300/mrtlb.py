@@ -42,6 +42,9 @@ EXPORTS = (
     "mrtlb_sync", "mrtlb_set_kernel", "mrtlb_step_count", "mrtlb_last_error",
     "mrtlb_destroy", "mrtlb_timing_begin", "mrtlb_timing_end", "mrtlb_launches_per_step",
     "mrtlb_reduce_noalloc",
+    "mrtlb_batch_create", "mrtlb_batch_step", "mrtlb_batch_sync", "mrtlb_batch_set_tiles",
+    "mrtlb_batch_get_tiles", "mrtlb_batch_set_graph_steps", "mrtlb_batch_tune", "mrtlb_batch_nodes",
+    "mrtlb_batch_last_error", "mrtlb_batch_destroy",
 )
 
 MRTLB_NOALLOC_MAX_NODES = 1 << 20
@@ -110,6 +113,20 @@ def load(path=LIB_PATH):
     lib.mrtlb_launches_per_step.argtypes = [P]
     lib.mrtlb_reduce_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                          ctypes.POINTER(ctypes.c_double)]
+    I = ctypes.POINTER(ctypes.c_int)
+    lib.mrtlb_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(P)]
+    lib.mrtlb_batch_step.argtypes = [P, ctypes.c_long]
+    lib.mrtlb_batch_sync.argtypes = [P]
+    lib.mrtlb_batch_set_tiles.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.mrtlb_batch_get_tiles.argtypes = [P, I, I, I, I]
+    lib.mrtlb_batch_set_graph_steps.argtypes = [P, ctypes.c_int]
+    lib.mrtlb_batch_tune.argtypes = [P, ctypes.c_char_p, ctypes.c_int, I, I]
+    lib.mrtlb_batch_nodes.argtypes = [P]
+    lib.mrtlb_batch_nodes.restype = ctypes.c_longlong
+    lib.mrtlb_batch_last_error.argtypes = [P]
+    lib.mrtlb_batch_last_error.restype = ctypes.c_char_p
+    lib.mrtlb_batch_destroy.argtypes = [P]
+    lib.mrtlb_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -223,6 +240,65 @@ def mrtlb_reduce_noalloc(f, nx, ny, precision, stream=None):
             "bad argument or size above the static scratch limit" if code == MRTLB_ERR_ARG
             else "CUDA error"))
     return np.array(out[:], dtype=np.float64)
+
+
+def _bcheck(code, b):
+    if code != MRTLB_OK:
+        msg = load().mrtlb_batch_last_error(b) if b else b""
+        raise MrtlbError(code, (msg.decode() if msg else "") or "batch call failed")
+
+
+def mrtlb_batch_create(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    b = ctypes.c_void_p()
+    code = load().mrtlb_batch_create(arr, len(ctxs), ctypes.byref(b))
+    if code != MRTLB_OK:
+        raise MrtlbError(code, {MRTLB_ERR_STATE: "every instance must be bound with TMA maps",
+                                MRTLB_ERR_ARG: "instances must share precision, stream and parity"}
+                         .get(code, "mrtlb_batch_create failed"))
+    return b
+
+
+def mrtlb_batch_step(b, nsteps):
+    _bcheck(load().mrtlb_batch_step(b, int(nsteps)), b)
+
+
+def mrtlb_batch_sync(b):
+    _bcheck(load().mrtlb_batch_sync(b), b)
+
+
+def mrtlb_batch_set_tiles(b, bx, seglen):
+    _bcheck(load().mrtlb_batch_set_tiles(b, int(bx), int(seglen)), b)
+
+
+def mrtlb_batch_get_tiles(b):
+    v = [ctypes.c_int() for _ in range(4)]
+    _bcheck(load().mrtlb_batch_get_tiles(b, *[ctypes.byref(x) for x in v]), b)
+    return tuple(x.value for x in v)  # (bx, seglen, ntiles, grid)
+
+
+def mrtlb_batch_set_graph_steps(b, steps):
+    _bcheck(load().mrtlb_batch_set_graph_steps(b, int(steps)), b)
+
+
+def mrtlb_batch_tune(b, cache_path=None, trial_steps=8):
+    bx = ctypes.c_int()
+    sl = ctypes.c_int()
+    path = cache_path.encode() if cache_path else None
+    _bcheck(load().mrtlb_batch_tune(b, path, int(trial_steps), ctypes.byref(bx), ctypes.byref(sl)), b)
+    return bx.value, sl.value
+
+
+def mrtlb_batch_nodes(b):
+    return load().mrtlb_batch_nodes(b)
+
+
+def mrtlb_batch_last_error(b):
+    return load().mrtlb_batch_last_error(b).decode()
+
+
+def mrtlb_batch_destroy(b):
+    load().mrtlb_batch_destroy(b)
 
 
 def mrtlb_launches_per_step(ctx):

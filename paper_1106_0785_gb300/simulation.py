@@ -105,3 +105,53 @@ class Simulation:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Many Simulations advanced together (mrtlb_batch_*).  The Simulations
+    stay usable for macros / get_f / reduce; they must outlive the batch."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        self.b = M.mrtlb_batch_create([s.ctx for s in self.sims])
+
+    def step(self, n=1):
+        M.mrtlb_batch_step(self.b, n)
+
+    def sync(self):
+        M.mrtlb_batch_sync(self.b)
+
+    def set_tiles(self, bx, seglen):
+        M.mrtlb_batch_set_tiles(self.b, bx, seglen)
+
+    @property
+    def tiles(self):
+        """(strip width, rows per segment, number of tiles, persistent grid)"""
+        return M.mrtlb_batch_get_tiles(self.b)
+
+    def set_graph_steps(self, n):
+        M.mrtlb_batch_set_graph_steps(self.b, n)
+
+    def tune(self, cache_path=None, trial_steps=8):
+        return M.mrtlb_batch_tune(self.b, cache_path, trial_steps)
+
+    @property
+    def nodes(self):
+        return M.mrtlb_batch_nodes(self.b)
+
+    def close(self):
+        if self.b is not None:
+            M.mrtlb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

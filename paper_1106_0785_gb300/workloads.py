@@ -147,3 +147,31 @@ def random_distributions(nx, ny, seed, lo=0.02, hi=0.2):
     """Positive random f of shape (16, ny, nx): a generic input for one step."""
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=(16, ny, nx))
+
+
+# ---------------------------------------------------------------------------
+# Batched set: Sod-type Riemann and Couette instances of uneven shapes
+# ---------------------------------------------------------------------------
+def batched_instances(n=64, precision="fp32", nx_range=(128, 2048), ny_range=(4, 256)):
+    """Instance i draws from numpy.random.default_rng(seed=i): NX ~ U{128..2048},
+    NY ~ U{4..256}, Pr ~ U[0.3, 3].  Even i: Sod-type tube, rho 1 | 0.125,
+    p 1 | 1/ratio with ratio ~ U[2, 20], dt = 1e-5, s5 = s6 = 1.5e4.  Odd i:
+    Couette channel, moving wall speed ~ U[0.1, 0.8], dt = 1e-4, s5 = s6 = 1e2.
+    s7 = s8 = Pr s5 in both.  Returns a list of (Config, fields)."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed=i)
+        nx = int(rng.integers(nx_range[0], nx_range[1] + 1))
+        ny = int(rng.integers(ny_range[0], ny_range[1] + 1))
+        Pr = float(rng.uniform(0.3, 3.0))
+        if i % 2 == 0:
+            ratio = float(rng.uniform(2.0, 20.0))
+            cfg, fields = sod(nx=nx, ny=ny, precision=precision, dt=1e-5, left=(1.0, 1.0),
+                              right=(0.125, (1.0 / ratio) / 0.125), s_visc=1.5e4,
+                              s_cond=Pr * 1.5e4, s_other=1e5)
+        else:
+            U = float(rng.uniform(0.1, 0.8))
+            cfg, fields = couette(Pr=Pr, nx=nx, ny=ny, precision=precision, dt=1e-4, U=U,
+                                  s_visc=1e2, s_other=1e3)
+        out.append((cfg, fields))
+    return out

@@ -1,0 +1,126 @@
+"""Batched stepping (many uneven grids, one launch per step, CUDA graphs,
+autotuned tiles) against the same instances stepped one by one, and against
+the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import equilibrium as oeq
+from oracle import fdlb
+from paper_1106_0785_gb300 import mrtlb as M
+from paper_1106_0785_gb300 import workloads
+from paper_1106_0785_gb300.simulation import Batch, Simulation
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances(precision):
+    """Six small instances: Sod-type tubes, Couette channels (NEE walls) and
+    an interface-with-shock grid, of uneven shapes with ragged strips."""
+    out = []
+    for nx, ny, right in ((300, 5, (0.125, 0.8)), (150, 9, (0.2, 2.0)), (257, 40, (0.5, 1.5))):
+        out.append(workloads.sod(nx=nx, ny=ny, precision=precision, right=right))
+    for nx, ny, Pr, U in ((130, 12, 0.5, 0.4), (257, 7, 2.0, 0.8), (64, 33, 1.3, 0.2)):
+        out.append(workloads.couette(Pr=Pr, nx=nx, ny=ny, precision=precision, U=U))
+    out.append(workloads.richtmyer_meshkov(nx=200, ny=36, precision=precision))
+    return out
+
+
+def _sims(insts, kernel=None):
+    sims = []
+    for cfg, fields in insts:
+        s = Simulation(cfg)
+        if kernel is not None:
+            s.set_kernel(kernel)
+        s.init_equilibrium(*fields)
+        sims.append(s)
+    return sims
+
+
+def _rel(a, b):
+    scale = np.abs(b).reshape(16, -1).max(1)
+    return (np.abs(a - b).reshape(16, -1).max(1) / scale).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_matches_instances_stepped_alone(cuda, precision):
+    insts = _instances(precision)
+    ref = _sims(insts, M.MRTLB_KERNEL_TILED)
+    for s in ref:
+        s.step(21)
+    want = [s.get_f() for s in ref]
+    sims = _sims(insts)
+    with Batch(sims) as b:
+        b.set_graph_steps(8)  # 2 graph replays, then 5 plain launches
+        b.step(21)
+        b.sync()
+    for s, w in zip(sims, want):
+        assert s.steps == 21
+        got = s.get_f()
+        assert _rel(got, w) < (1e-13 if precision == "fp64" else 1e-6)
+
+
+def test_batch_fp64_matches_oracle(cuda):
+    insts = _instances("fp64")[2:5]
+    sims = _sims(insts)
+    with Batch(sims) as b:
+        b.step(12)
+        b.sync()
+    for (cfg, (rho, ux, uy, T)), s in zip(insts, sims):
+        sides = tuple(fdlb.Side({"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW,
+                                 "wall": fdlb.WALL}[k], a, c, t) for k, a, c, t in cfg.bc)
+        p = fdlb.Params(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt, s=np.asarray(cfg.s),
+                        sides=sides)
+        ref = fdlb.run(fdlb.prepare(oeq.feq(rho, ux, uy, T), p), p, 12)
+        assert _rel(s.get_f(), ref) < 1e-11
+
+
+def test_tile_shapes_give_identical_results(cuda):
+    insts = _instances("fp32")
+    res = []
+    for bx, sl in ((128, 32), (64, 8), (128, 5)):
+        sims = _sims(insts)
+        with Batch(sims) as b:
+            b.set_tiles(bx, sl)
+            assert b.tiles[:2] == (bx, sl)
+            b.step(9)
+            b.sync()
+        res.append([s.get_f() for s in sims])
+    for other in res[1:]:
+        for a, c in zip(res[0], other):
+            assert np.array_equal(a, c)  # the per-node arithmetic does not depend on the tiling
+
+
+def test_tune_restores_state_and_uses_its_cache(cuda, tmp_path):
+    insts = _instances("fp32")
+    sims = _sims(insts)
+    before = [s.get_f() for s in sims]
+    cache = str(tmp_path / "tune.txt")
+    with Batch(sims) as b:
+        bx, sl = b.tune(cache, trial_steps=3)
+        assert b.tiles[:2] == (bx, sl)
+        after = [s.get_f() for s in sims]
+        for x, y in zip(before, after):
+            assert np.array_equal(x, y)
+        lines = open(cache).read().split("\n")
+        assert len([ln for ln in lines if ln.strip()]) == 1
+        assert b.tune(cache, trial_steps=3) == (bx, sl)  # cache hit
+        assert len([ln for ln in open(cache).read().split("\n") if ln.strip()]) == 1
+        b.step(4)
+        b.sync()
+
+
+def test_batch_requires_matching_instances(cuda):
+    a, _ = workloads.sod(nx=130, ny=5, precision="fp32")
+    c, _ = workloads.sod(nx=130, ny=5, precision="fp64")
+    s1, s2 = Simulation(a), Simulation(c)
+    with pytest.raises(M.MrtlbError):
+        Batch([s1, s2])
+    s3 = Simulation(a)
+    s3.step(1)
+    with pytest.raises(M.MrtlbError):
+        Batch([s1, s3])  # different buffer parity
+    with Batch([s1, Simulation(a)]) as b:
+        s1.step(1)  # stepped outside the batch
+        with pytest.raises(M.MrtlbError) as ei:
+            b.step(1)
+        assert ei.value.code == M.MRTLB_ERR_STATE
