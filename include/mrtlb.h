@@ -232,6 +232,44 @@ long long mrtlb_batch_nodes(const mrtlb_batch* b);
 const char* mrtlb_batch_last_error(const mrtlb_batch* b);
 void mrtlb_batch_destroy(mrtlb_batch* b);
 
+/* Replace / read the relaxation rates s_1..s_16 (same limits as create).
+ * Batches made earlier keep the rates they copied. */
+int mrtlb_set_rates(mrtlb_ctx* ctx, const double* s);
+int mrtlb_get_rates(const mrtlb_ctx* ctx, double* s);
+
+/* ------------------------------------------------------------------------
+ * Adjoint (reverse mode) of K time steps.  The paper has no adjoint; this is
+ * the exact transpose of the discrete step above (Sec. II-III as
+ * implemented: Lax-Wendroff advection, collision with the modified
+ * energy-flux terms, NEE walls, periodic and outflow ghosts), for
+ * gradients of a loss on the final state with respect to the initial state
+ * and the relaxation rates.  Equilibrium versions 1 and 2.
+ *
+ * mrtlb_adjoint_forward(ctx, K): advances the context K steps from its
+ *   current state f^0 (like mrtlb_step) and stores a checkpoint every
+ *   S = ceil(sqrt(K)) steps (library-owned device memory: about
+ *   (K/S + S + 4) state buffers, freed by mrtlb_adjoint_release or destroy).
+ * mrtlb_adjoint_backward(ctx, dL_dmacros, dL_dfK, dL_ds, dL_df0): seeds
+ *   with dL/d(rho, u_x, u_y, T) of the final state as mrtlb_macros returns it
+ *   (device FP64 [4][ny][nx], or NULL) and/or dL/df^K of the state as
+ *   mrtlb_get_f returns it (device FP64 [16][ny][nx], or NULL); recomputes
+ *   each segment from its checkpoint on separate buffers (the context keeps
+ *   f^K) and runs the adjoint steps back to f^0.  Outputs: dL_ds[16] (host;
+ *   entries 5..16 of the paper's s, 0-based 4..15, accumulated in FP64;
+ *   0..3 are zero since those rates have no effect) and dL/df^0 (device FP64
+ *   [16][ny][nx], or NULL).  Synchronises.
+ * mrtlb_equilibrium_adjoint: for a state initialised by
+ *   mrtlb_init_equilibrium from (rho, u_x, u_y, T) (device FP64 [ny][nx]),
+ *   maps dL/df (device FP64 [16][ny][nx]) to dL/d(rho, u_x, u_y, T)
+ *   (device FP64 [ny][nx] each).  Synchronises. */
+int mrtlb_adjoint_forward(mrtlb_ctx* ctx, long K);
+int mrtlb_adjoint_backward(mrtlb_ctx* ctx, const double* dL_dmacros, const double* dL_dfK,
+                           double dL_ds[16], double* dL_df0);
+int mrtlb_adjoint_release(mrtlb_ctx* ctx);
+int mrtlb_equilibrium_adjoint(mrtlb_ctx* ctx, const double* dL_df, const double* rho,
+                              const double* ux, const double* uy, const double* T,
+                              double* dL_drho, double* dL_dux, double* dL_duy, double* dL_dT);
+
 /* Number of time steps taken since the last init/set. */
 long mrtlb_step_count(const mrtlb_ctx* ctx);
 

@@ -1,0 +1,42 @@
+"""torch.autograd.Function over K steps of the MRT FD-LB model.
+
+Forward: the initial state is the equilibrium of (rho0, ux0, uy0, T0)
+(device FP64 [ny][nx] tensors), the rates s (16) are set on the context,
+K steps run with sqrt(K) checkpoints (mrtlb_adjoint_forward), and the final
+macroscopic fields come back as device FP64 tensors.  Backward: the
+hand-written adjoint kernels (mrtlb_adjoint_backward) give dL/ds and
+dL/df0, and mrtlb_equilibrium_adjoint maps dL/df0 to the initial fields, so
+torch can carry the chain on to whatever produced them (e.g. an interface
+shape).  There is no CPU path: the library's kernels do all of the work.
+"""
+import torch
+
+
+class MRTLBRun(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rho0, ux0, uy0, T0, s, sim, K):
+        fields = [a.detach().to(sim.device, torch.float64).contiguous() for a in (rho0, ux0, uy0, T0)]
+        sim.set_rates(s.detach().cpu().double().numpy())
+        sim.init_equilibrium(*fields)
+        sim.adjoint_forward(K)
+        rho, ux, uy, T = sim.macros(on_device=True)
+        ctx.sim = sim
+        ctx.save_for_backward(*fields)
+        ctx.s_device = s.device
+        return rho, ux, uy, T
+
+    @staticmethod
+    def backward(ctx, g_rho, g_ux, g_uy, g_T):
+        sim = ctx.sim
+        zeros = lambda: torch.zeros((sim.cfg.ny, sim.cfg.nx), dtype=torch.float64, device=sim.device)
+        seed = torch.stack([g if g is not None else zeros() for g in (g_rho, g_ux, g_uy, g_T)])
+        ds, df0 = sim.adjoint_backward(dL_dmacros=seed)
+        rho0, ux0, uy0, T0 = ctx.saved_tensors
+        d_rho, d_ux, d_uy, d_T = sim.equilibrium_adjoint(df0, rho0, ux0, uy0, T0)
+        return d_rho, d_ux, d_uy, d_T, torch.as_tensor(ds, device=ctx.s_device), None, None
+
+
+def run(sim, rho0, ux0, uy0, T0, s, K):
+    """Final (rho, ux, uy, T) after K steps, differentiable with respect to the
+    initial fields and the 16 rates s (a torch tensor)."""
+    return MRTLBRun.apply(rho0, ux0, uy0, T0, s, sim, K)

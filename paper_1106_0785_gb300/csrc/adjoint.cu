@@ -1,0 +1,631 @@
+// adjoint.cu - reverse (adjoint) of the time step, checkpointed over K steps.
+//
+// Forward step, per advanced node r (Sec. II-III as implemented):
+//   f1(r) = ft(r) + sum_n k_qn (ft(r + e_n) - ft(r)) - C(ft(r), grad u(r))
+// where ft = B(f) is the state with walls refilled (NEE) and ghosts filled.
+// Given lambda = dL/df1 (zero at non-advanced nodes) the adjoint step is
+//   lambda_prev = B^T J^T lambda,
+// gathered per node p of the padded grid:
+//   (a) Lax-Wendroff: (1 - sum_n k_qn) lambda_q(p) + sum_n k_qn lambda_q(p - e_n);
+//   (b) collision at p: -(dC/df(p))^T lambda(p) (equilibrium, temperature
+//       and the modification's local factors rho T u, all through M);
+//   (c) the modification at the four neighbours r, through u(p) in their
+//       central differences: gbar_shear(r), gbar_strain(r) (dL/d of the two
+//       strain combinations at r) from a first pass, then u = j / rho at p.
+// B^T adds each ghost's adjoint to the node it mirrors and maps each wall
+// node's adjoint through the Jacobian of the NEE fill to its fluid
+// neighbour (walls themselves get zero).  Gradients with respect to the
+// rates s_5..s_16 accumulate in FP64.
+//
+// K steps use sqrt(K) checkpointing: adjoint_forward stores the state every
+// S = ceil(sqrt(K)) steps; backward recomputes each segment's S states on
+// separate work buffers (the context keeps f^K) and runs the adjoint steps
+// through it in reverse.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "adjoint.cuh"
+#include "ctx.h"
+
+namespace mrtlb {
+namespace {
+
+template <typename R>
+struct AdjCoef {
+  Coef<R> c;
+  R dt;
+  R s5, s6, s7, s8;
+};
+
+template <typename R>
+__device__ __forceinline__ bool advanced(const Layout& L, int i, int j) {
+  return i >= L.i0 && i < L.i1 && j >= L.j0 && j < L.j1;
+}
+
+template <typename R>
+__device__ __forceinline__ void load16(const R* f, long long plane, long long at, R g[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) g[q] = f[q * plane + at];
+}
+
+// Pass 1: adjoints of the two strain combinations of the modification at
+// every advanced node r (zero elsewhere, from the buffer's initial clear).
+template <typename R>
+__global__ void adj_gbar_kernel(const R* __restrict__ ft, const R* __restrict__ lam, R* gsh, R* gst,
+                                Layout L, AdjCoef<R> a) {
+  const int i = L.i0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = L.j0 + blockIdx.y;
+  if (i >= L.i1 || j >= L.j1) return;
+  const long long at = L.node(i, j);
+  R g[16], lb[16], cb[16];
+  load16(ft, L.plane, at, g);
+  load16(lam, L.plane, at, lb);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) lb[q] = -lb[q];  // dL/dC = -lambda
+  inverse_T(a.c, lb, cb, false);
+  R rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const R ir = R(1) / rho;
+  const R ux = jx * ir, uy = jy * ir;
+  const R P = rho * temperature(rho, jx, jy, e, ir);
+  gsh[at] = cb[6] * a.c.mod[0] * P * ux + cb[7] * a.c.mod[3] * P * uy;
+  gst[at] = cb[6] * a.c.mod[1] * P * uy + cb[7] * a.c.mod[2] * P * ux;
+}
+
+template <typename R>
+__device__ __forceinline__ R gbar_at(const R* gb, const Layout& L, int i, int j) {
+  if (i < -1 || i > L.nx || j < -1 || j > L.ny) return R(0);
+  return gb[L.node(i, j)];
+}
+
+template <typename R>
+__device__ __forceinline__ void velocity_at(const R* ft, const Layout& L, int i, int j, R& ux, R& uy) {
+  R g[16];
+  load16(ft, L.plane, L.node(i, j), g);
+  R rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const R ir = R(1) / rho;
+  ux = jx * ir;
+  uy = jy * ir;
+}
+
+// Pass 2: lambda~(p) for every node of [-1, nx] x [-1, ny] (corners excluded)
+// plus the rate gradients of the advanced nodes.
+template <typename R>
+__global__ void __launch_bounds__(128) adj_core_kernel(const R* __restrict__ ft, const R* __restrict__ lam,
+                                                       const R* __restrict__ gsh, const R* __restrict__ gst,
+                                                       R* __restrict__ out, Layout L, AdjCoef<R> a,
+                                                       double* gacc) {
+  const int i = -1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = -1 + (int)blockIdx.y;
+  double G[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) G[k] = 0.0;
+  const bool inside = i <= L.nx && j <= L.ny && !((i < 0 || i >= L.nx) && (j < 0 || j >= L.ny));
+  if (inside) {
+    const Coef<R>& c = a.c;
+    const long long P = L.plane;
+    const long long at = L.node(i, j);
+    R g[16], lt[16];
+    load16(ft, P, at, g);
+    R rho, jx, jy, e;
+    conserved(g, rho, jx, jy, e);
+    // (ghost rows behind walls are never read by an advanced node and may be empty)
+    const R ir = (rho > R(0)) ? R(1) / rho : R(0);
+    const R ux = jx * ir, uy = jy * ir;
+    const R T = temperature(rho, jx, jy, e, ir);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) lt[q] = R(0);
+    if (advanced<R>(L, i, j)) {
+      R lp[16];
+      load16(lam, P, at, lp);
+      // (a) the node's own Lax-Wendroff weight
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        R w = R(1);
+        if (vx_of(q) != 0) w -= c.lw[q][0] + c.lw[q][1];
+        if (vy_of(q) != 0) w -= c.lw[q][2] + c.lw[q][3];
+        lt[q] = w * lp[q];
+      }
+      // forward quantities of the collision at p
+      R uxE, uyE, uxW, uyW, uxN, uyN, uxS, uyS;
+      velocity_at(ft, L, i + 1, j, uxE, uyE);
+      velocity_at(ft, L, i - 1, j, uxW, uyW);
+      velocity_at(ft, L, i, j + 1, uxN, uyN);
+      velocity_at(ft, L, i, j - 1, uxS, uyS);
+      const R shear = (uxE - uxW) * c.inv2dx - (uyN - uyS) * c.inv2dy;
+      const R strain = (uyE - uyW) * c.inv2dx + (uxN - uxS) * c.inv2dy;
+      Harm<R> h;
+      harmonics(g, h);
+      R m[16], eq[16];
+      moments(h, m);
+      equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eq);
+      const R Pp = rho * T;
+      // (b) collision transpose
+      R Cb[16], cb[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) Cb[q] = -lp[q];
+      inverse_T(c, Cb, cb, false);
+      R mb[16], eqb[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        mb[k] = (k >= 4) ? c.rate[k] * cb[k] : R(0);
+        eqb[k] = (k >= 4) ? -c.rate[k] * cb[k] : R(0);
+      }
+      EqIn<R> x{rho, ir, jx, jy, e, ux, uy, T};
+      EqIn<R> gi{R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+      if (c.modified) {
+        const R Pb = cb[6] * (c.mod[0] * ux * shear + c.mod[1] * uy * strain) +
+                     cb[7] * (c.mod[2] * ux * strain + c.mod[3] * uy * shear);
+        gi.ux += cb[6] * c.mod[0] * Pp * shear + cb[7] * c.mod[2] * Pp * strain;
+        gi.uy += cb[6] * c.mod[1] * Pp * strain + cb[7] * c.mod[3] * Pp * shear;
+        gi.rho += Pb * T;
+        gi.T += Pb * rho;
+      }
+      equilibrium_T(c, x, eqb, gi);
+      R rb, jxb, jyb, eb;
+      chain_primitive(x, gi, rb, jxb, jyb, eb);
+      mb[0] += rb;
+      mb[1] += jxb;
+      mb[2] += jyb;
+      mb[3] += eb;
+      Harm<R> hb;
+      moments_T(mb, hb);
+      R fb[16];
+      harmonics_T(hb, fb);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) lt[q] += fb[q];
+      // rate gradients: d f1 / d s_k through dt s_k (m_k - eq_k) and the
+      // modification factors dt (s7/s5 - 1), ... (dL/dC = -lambda)
+      const double dt = (double)a.dt;
+#pragma unroll
+      for (int k = 4; k < 16; ++k) G[k] = dt * (double)cb[k] * ((double)m[k] - (double)eq[k]);
+      if (c.modified) {
+        const double A0 = (double)Pp * ux * shear, A1 = (double)Pp * uy * strain;
+        const double A2 = (double)Pp * ux * strain, A3 = (double)Pp * uy * shear;
+        const double s5 = a.s5, s6 = a.s6, s7 = a.s7, s8 = a.s8;
+        G[6] += (double)cb[6] * dt * (A0 / s5 + A1 / s6);
+        G[7] += (double)cb[7] * dt * (A2 / s6 + A3 / s5);
+        G[4] -= dt * ((double)cb[6] * A0 * s7 / (s5 * s5) + (double)cb[7] * A3 * s8 / (s5 * s5));
+        G[5] -= dt * ((double)cb[6] * A1 * s7 / (s6 * s6) + (double)cb[7] * A2 * s8 / (s6 * s6));
+      }
+    }
+    // (a) neighbours' Lax-Wendroff weights on p
+    const int nbi[4] = {i - 1, i + 1, i, i};  // r = p - e_x (uses kE), p + e_x (kW), p - e_y (kN), p + e_y (kS)
+    const int nbj[4] = {j, j, j - 1, j + 1};
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      if (!advanced<R>(L, nbi[n], nbj[n])) continue;
+      const long long ar = L.node(nbi[n], nbj[n]);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (n < 2 && vx_of(q) == 0) continue;
+        if (n >= 2 && vy_of(q) == 0) continue;
+        lt[q] += c.lw[q][n] * lam[q * P + ar];
+      }
+    }
+    // (c) the modification at the neighbours, through u(p)
+    if (c.modified) {
+      const R uxb = c.inv2dx * (gbar_at(gsh, L, i - 1, j) - gbar_at(gsh, L, i + 1, j)) +
+                    c.inv2dy * (gbar_at(gst, L, i, j - 1) - gbar_at(gst, L, i, j + 1));
+      const R uyb = c.inv2dx * (gbar_at(gst, L, i - 1, j) - gbar_at(gst, L, i + 1, j)) -
+                    c.inv2dy * (gbar_at(gsh, L, i, j - 1) - gbar_at(gsh, L, i, j + 1));
+#pragma unroll
+      for (int q = 0; q < 16; ++q) lt[q] += (uxb * (R(vx_of(q)) - ux) + uyb * (R(vy_of(q)) - uy)) * ir;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) out[q * P + at] = lt[q];
+  }
+  // block reduction of the rate gradients, one atomic per warp
+#pragma unroll
+  for (int k = 4; k < 16; ++k) {
+    double v = G[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(gacc + k, v);
+  }
+}
+
+// B^T, ghosts: every edge node collects the adjoints of the ghost cells that
+// mirror it; the ghost cells are cleared.
+template <typename R>
+__global__ void adj_ghosts_kernel(R* lam, Layout L) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int perim = 2 * L.nx + 2 * L.ny;
+  if (t >= perim) return;
+  int i, j;
+  if (t < L.nx) { i = t; j = 0; }
+  else if (t < 2 * L.nx) { i = t - L.nx; j = L.ny - 1; }
+  else if (t < 2 * L.nx + L.ny) { i = 0; j = t - 2 * L.nx; }
+  else { i = L.nx - 1; j = t - 2 * L.nx - L.ny; }
+  // a node on two edges appears twice; let the first appearance do the work
+  if (t >= 2 * L.nx && (j == 0 || j == L.ny - 1)) return;
+  if (t >= L.nx && t < 2 * L.nx && L.ny == 1) return;
+  if (t >= 2 * L.nx + L.ny && L.nx == 1) return;
+  const GhostTargets g = ghost_targets(L, i, j);
+  R* p = lam + L.node(i, j);
+  for (int s = 0; s < 4; ++s) {
+    if (!g.w[s]) continue;
+    for (int q = 0; q < 16; ++q) p[q * L.plane] += p[q * L.plane + g.off[s]];
+  }
+}
+
+template <typename R>
+__global__ void adj_clear_ghosts_kernel(R* lam, Layout L) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  R* lq = lam + q * L.plane;
+  if (t < L.ny + 2) {
+    lq[(long long)t * L.pitch + L.xoff - 1] = R(0);
+    lq[(long long)t * L.pitch + L.xoff + L.nx] = R(0);
+  }
+  if (t < L.nx) {
+    lq[L.xoff + t] = R(0);
+    lq[(long long)(L.ny + 1) * L.pitch + L.xoff + t] = R(0);
+  }
+}
+
+// B^T, walls on one side: the wall node w was NEE(f(a)) of its fluid
+// neighbour a: lambda(a) += (dNEE/df(a))^T lambda~(w), lambda(w) = 0.
+template <typename R>
+__global__ void adj_walls_kernel(R* lam, const R* __restrict__ ft, Layout L, Coef<double> c, Walls w, int side) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = (side < 2) ? L.ny : L.nx;
+  if (k >= n) return;
+  int i, j, ia, ja;
+  if (side == 0) { i = 0; j = k; ia = 1; ja = k; }
+  else if (side == 1) { i = L.nx - 1; j = k; ia = L.nx - 2; ja = k; }
+  else if (side == 2) { i = k; j = 0; ia = k; ja = 1; }
+  else { i = k; j = L.ny - 1; ia = k; ja = L.ny - 2; }
+  const long long P = L.plane, aw = L.node(i, j), aa = L.node(ia, ja);
+  double v[16], g[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    v[q] = (double)lam[q * P + aw];
+    g[q] = (double)ft[q * P + aa];
+  }
+  double rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const double ir = 1.0 / rho;
+  const double ux = jx * ir, uy = jy * ir;
+  const double T = temperature(rho, jx, jy, e, ir);
+  // NEE(g) = g + M^-1 (eq(rho, rho u_w, e_w, u_w, T_w) - eq(rho, j, e, u, T))
+  double db[16];
+  inverse_T(c, v, db, true);
+  const double uwx = w.ux[side], uwy = w.uy[side], Tw = w.T[side];
+  const double kw = Tw + 0.5 * (uwx * uwx + uwy * uwy);
+  EqIn<double> xw{rho, ir, rho * uwx, rho * uwy, rho * kw, uwx, uwy, Tw};
+  EqIn<double> gw{0, 0, 0, 0, 0, 0, 0, 0};
+  equilibrium_T(c, xw, db, gw);
+  double rbw = gw.rho - gw.ir * ir * ir + gw.jx * uwx + gw.jy * uwy + gw.e * kw;
+  double ndb[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) ndb[q] = -db[q];
+  EqIn<double> xa{rho, ir, jx, jy, e, ux, uy, T};
+  EqIn<double> ga{0, 0, 0, 0, 0, 0, 0, 0};
+  equilibrium_T(c, xa, ndb, ga);
+  double rb, jxb, jyb, eb;
+  chain_primitive(xa, ga, rb, jxb, jyb, eb);
+  rb += rbw;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const double vx = vx_of(q), vy = vy_of(q);
+    const double add = v[q] + rb + jxb * vx + jyb * vy + eb * 0.5 * (vx * vx + vy * vy);
+    lam[q * P + aa] = (R)((double)lam[q * P + aa] + add);
+    lam[q * P + aw] = R(0);
+  }
+}
+
+// Seed: lambda = (d(rho, u_x, u_y, T)/df)^T (dL/d macros) on every node.
+template <typename R>
+__global__ void adj_seed_macros_kernel(const R* __restrict__ ft, const double* __restrict__ seed, R* lam,
+                                       Layout L) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= L.nx) return;
+  const long long n = (long long)L.nx * L.ny, t = (long long)j * L.nx + i, at = L.node(i, j);
+  double g[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) g[q] = (double)ft[q * L.plane + at];
+  double rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const double ir = 1.0 / rho;
+  EqIn<double> x{rho, ir, jx, jy, e, jx * ir, jy * ir, temperature(rho, jx, jy, e, ir)};
+  EqIn<double> gi{seed[t], 0, 0, 0, 0, seed[n + t], seed[2 * n + t], seed[3 * n + t]};
+  double rb, jxb, jyb, eb;
+  chain_primitive(x, gi, rb, jxb, jyb, eb);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const double vx = vx_of(q), vy = vy_of(q);
+    lam[q * L.plane + at] = (R)(rb + jxb * vx + jyb * vy + eb * 0.5 * (vx * vx + vy * vy));
+  }
+}
+
+// Dense FP64 [16][ny][nx] <-> padded lambda: mode 0 sets lambda from the
+// dense array, 1 writes lambda to it, 2 adds the dense array to lambda.
+template <typename R>
+__global__ void adj_dense_kernel(R* lam, double* dense, Layout L, int mode) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, q = blockIdx.z;
+  if (i >= L.nx) return;
+  const long long d = ((long long)q * L.ny + j) * L.nx + i, p = q * L.plane + L.node(i, j);
+  if (mode == 1) dense[d] = (double)lam[p];
+  else if (mode == 0) lam[p] = (R)dense[d];
+  else lam[p] = (R)((double)lam[p] + dense[d]);
+}
+
+// dL/d(rho, u_x, u_y, T) of an equilibrium initial state f = M^-1 f^eq from
+// dL/df (dense FP64), all in FP64.
+__global__ void eq_adjoint_kernel(const double* __restrict__ lamd, const double* __restrict__ rho_in,
+                                  const double* __restrict__ ux_in, const double* __restrict__ uy_in,
+                                  const double* __restrict__ T_in, double* orho, double* oux, double* ouy,
+                                  double* oT, long long n, Coef<double> c) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double v[16], eqb[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = lamd[q * n + t];
+  inverse_T(c, v, eqb, true);
+  const double rho = rho_in[t], ux = ux_in[t], uy = uy_in[t], T = T_in[t];
+  const double ir = 1.0 / rho, k = T + 0.5 * (ux * ux + uy * uy);
+  EqIn<double> x{rho, ir, rho * ux, rho * uy, rho * k, ux, uy, T};
+  EqIn<double> g{0, 0, 0, 0, 0, 0, 0, 0};
+  equilibrium_T(c, x, eqb, g);
+  // inputs of the equilibrium as functions of (rho, u, T)
+  orho[t] = g.rho - g.ir * ir * ir + g.jx * ux + g.jy * uy + g.e * k;
+  oux[t] = g.ux + g.jx * rho + g.e * rho * ux;
+  ouy[t] = g.uy + g.jy * rho + g.e * rho * uy;
+  oT[t] = g.T + g.e * rho;
+}
+
+}  // namespace
+}  // namespace mrtlb
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct mrtlb_adjoint_state {
+  long K = 0, S = 0;
+  std::vector<void*> ckpt;   // states at t = 0, S, 2S, ... (padded)
+  void* seg = nullptr;       // S states of the segment being reversed
+  void* work[2] = {nullptr, nullptr};
+  TiledPlan plan{};
+  void* lam[2] = {nullptr, nullptr};
+  void* gsh = nullptr;       // one padded plane each
+  void* gst = nullptr;
+  double* gacc = nullptr;
+};
+
+namespace {
+
+int afail(mrtlb_ctx* c, int code, const char* msg) {
+  c->last_error = msg;
+  return code;
+}
+
+#define ACK(call, what)                                                              \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      c->last_error = std::string(what) + ": " + cudaGetErrorString(e_);              \
+      return MRTLB_ERR_CUDA;                                                         \
+    }                                                                                \
+  } while (0)
+
+void release(mrtlb_adjoint_state* a) {
+  if (!a) return;
+  for (void* p : a->ckpt) cudaFree(p);
+  a->ckpt.clear();
+  for (void* p : {a->seg, a->work[0], a->work[1], a->lam[0], a->lam[1], a->gsh, a->gst, (void*)a->gacc})
+    if (p) cudaFree(p);
+  delete a;
+}
+
+template <typename R>
+AdjCoef<R> adj_coef(const mrtlb_ctx* c, const Coef<R>& k) {
+  AdjCoef<R> a;
+  a.c = k;
+  a.dt = (R)c->p.dt;
+  a.s5 = (R)c->s[4];
+  a.s6 = (R)c->s[5];
+  a.s7 = (R)c->s[6];
+  a.s8 = (R)c->s[7];
+  return a;
+}
+
+// one adjoint step: lam_in (dL/df^{n+1}) -> lam_out (dL/df^n), ft = B(f^n)
+template <typename R>
+void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, const R* ft, const R* lam_in, R* lam_out,
+                  const Coef<R>& k, cudaStream_t st) {
+  const Layout& L = c->L;
+  const AdjCoef<R> ac = adj_coef<R>(c, k);
+  const size_t plane_bytes = (size_t)L.plane * sizeof(R);
+  cudaMemsetAsync(a->gsh, 0, plane_bytes, st);
+  cudaMemsetAsync(a->gst, 0, plane_bytes, st);
+  const int ni = L.i1 - L.i0, nj = L.j1 - L.j0;
+  if (ni > 0 && nj > 0) {
+    dim3 g1((ni + 127) / 128, nj);
+    adj_gbar_kernel<R><<<g1, 128, 0, st>>>(ft, lam_in, (R*)a->gsh, (R*)a->gst, L, ac);
+  }
+  dim3 g2((L.nx + 2 + 127) / 128, L.ny + 2);
+  adj_core_kernel<R><<<g2, 128, 0, st>>>(ft, lam_in, (const R*)a->gsh, (const R*)a->gst, lam_out, L, ac,
+                                         a->gacc);
+  const int perim = 2 * L.nx + 2 * L.ny;
+  adj_ghosts_kernel<R><<<(perim + 127) / 128, 128, 0, st>>>(lam_out, L);
+  dim3 g3((std::max(L.nx, L.ny + 2) + 255) / 256, 16);
+  adj_clear_ghosts_kernel<R><<<g3, 256, 0, st>>>(lam_out, L);
+  for (int s = 0; s < 4; ++s)
+    if (L.bc[s] == BC_WALL) {
+      const int n = (s < 2) ? L.ny : L.nx;
+      adj_walls_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(lam_out, ft, L, c->c64, c->walls, s);
+    }
+}
+
+template <typename R>
+void walls_only(mrtlb_ctx* c, R* f, cudaStream_t st) {
+  launch_walls<R>(f, c->L, c->c64, c->walls, st);
+}
+
+template <typename R>
+void step_on(mrtlb_ctx* c, mrtlb_adjoint_state* a, int cur, const Coef<R>& k, cudaStream_t st) {
+  R* fin = (R*)a->work[cur];
+  R* fout = (R*)a->work[cur ^ 1];
+  walls_only<R>(c, fin, st);
+  if (a->plan.ok) launch_step_tiled<R>(a->plan, cur, c->L, k, c->err, st, fout);
+  else launch_step_plain<R>(fin, fout, c->L, k, c->err, st);
+}
+
+template <typename R>
+int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, double* dL_ds,
+                  double* dL_df0) {
+  mrtlb_adjoint_state* a = c->adj;
+  const Layout& L = c->L;
+  cudaStream_t st = c->stream;
+  const Coef<R>& k = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&c->c32 : (const void*)&c->c64);
+  const size_t sb = c->state_bytes;
+  R* lam0 = (R*)a->lam[0];
+  R* lam1 = (R*)a->lam[1];
+  ACK(cudaMemsetAsync(lam0, 0, sb, st), "clear");
+  ACK(cudaMemsetAsync(lam1, 0, sb, st), "clear");
+  ACK(cudaMemsetAsync(a->gacc, 0, 16 * sizeof(double), st), "clear");
+  // seed on B(f^K)
+  R* fK = (R*)c->f[c->cur];
+  launch_bc<R>(fK, L, c->c64, c->walls, st);
+  dim3 gs((L.nx + 127) / 128, L.ny);
+  if (dL_dmacros) adj_seed_macros_kernel<R><<<gs, 128, 0, st>>>(fK, dL_dmacros, lam0, L);
+  if (dL_dfK) {  // a direct seed on the state (as mrtlb_get_f returns it); added to the macro seed
+    dim3 gd((L.nx + 127) / 128, L.ny, 16);
+    adj_dense_kernel<R><<<gd, 128, 0, st>>>(lam0, (double*)dL_dfK, L, dL_dmacros ? 2 : 0);
+  }
+  // walls of B^T for the seed
+  for (int s = 0; s < 4; ++s)
+    if (L.bc[s] == BC_WALL) {
+      const int n = (s < 2) ? L.ny : L.nx;
+      adj_walls_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(lam0, fK, L, c->c64, c->walls, s);
+    }
+  ACK(cudaGetLastError(), "adjoint seed");
+  R* lin = lam0;
+  R* lout = lam1;
+  const long K = a->K, S = a->S;
+  const long nseg = (K + S - 1) / S;
+  for (long sgi = nseg - 1; sgi >= 0; --sgi) {
+    const long t0 = sgi * S;
+    const long len = std::min(S, K - t0);
+    // recompute the segment's states B(f^{t0}), ..., B(f^{t0+len-1})
+    ACK(cudaMemcpyAsync(a->work[0], a->ckpt[sgi], sb, cudaMemcpyDeviceToDevice, st), "restore checkpoint");
+    int cur = 0;
+    for (long n = 0; n < len; ++n) {
+      walls_only<R>(c, (R*)a->work[cur], st);
+      ACK(cudaMemcpyAsync((char*)a->seg + (size_t)n * sb, a->work[cur], sb, cudaMemcpyDeviceToDevice, st),
+          "store segment state");
+      if (n + 1 < len) {
+        step_on<R>(c, a, cur, k, st);
+        cur ^= 1;
+      }
+    }
+    for (long n = len - 1; n >= 0; --n) {
+      const R* ft = (const R*)((char*)a->seg + (size_t)n * sb);
+      adjoint_step<R>(c, a, ft, lin, lout, k, st);
+      std::swap(lin, lout);
+      ACK(cudaMemsetAsync(lout, 0, sb, st), "clear");
+    }
+  }
+  ACK(cudaGetLastError(), "adjoint steps");
+  if (dL_df0) {
+    dim3 gd((L.nx + 127) / 128, L.ny, 16);
+      adj_dense_kernel<R><<<gd, 128, 0, st>>>(lin, dL_df0, L, 1);
+  }
+  if (dL_ds) ACK(cudaMemcpyAsync(dL_ds, a->gacc, 16 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy grads");
+  ACK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  return MRTLB_OK;
+}
+
+}  // namespace
+
+extern "C" int mrtlb_adjoint_forward(mrtlb_ctx* c, long K) {
+  if (!c) return MRTLB_ERR_ARG;
+  if (!c->f[0] || !c->f[1]) return afail(c, MRTLB_ERR_STATE, "bind state buffers first");
+  if (K < 0) return afail(c, MRTLB_ERR_ARG, "K < 0");
+  if (c->p.eq_version == 3)
+    return afail(c, MRTLB_ERR_UNSUPPORTED, "the adjoint covers equilibrium versions 1 and 2");
+  release(c->adj);
+  c->adj = new mrtlb_adjoint_state();
+  mrtlb_adjoint_state* a = c->adj;
+  a->K = K;
+  a->S = std::max(1L, (long)std::ceil(std::sqrt((double)std::max(K, 1L))));
+  const size_t sb = c->state_bytes;
+  const long nck = std::max(1L, (K + a->S - 1) / a->S);
+  cudaStream_t st = c->stream;
+  for (long i = 0; i < nck; ++i) {
+    void* p = nullptr;
+    ACK(cudaMalloc(&p, sb), "cudaMalloc(checkpoint)");
+    a->ckpt.push_back(p);
+  }
+  ACK(cudaMalloc(&a->seg, sb * (size_t)a->S), "cudaMalloc(segment)");
+  for (int b = 0; b < 2; ++b) {
+    ACK(cudaMalloc(&a->work[b], sb), "cudaMalloc(work)");
+    ACK(cudaMemsetAsync(a->work[b], 0, sb, st), "clear");
+    ACK(cudaMalloc(&a->lam[b], sb), "cudaMalloc(lambda)");
+  }
+  const size_t pb = (size_t)c->L.plane * c->esize;
+  ACK(cudaMalloc(&a->gsh, pb), "cudaMalloc(gbar)");
+  ACK(cudaMalloc(&a->gst, pb), "cudaMalloc(gbar)");
+  ACK(cudaMalloc((void**)&a->gacc, 16 * sizeof(double)), "cudaMalloc(grad)");
+  plan_tiled(c->L, (int)c->esize, a->work[0], a->work[1], &a->plan);
+  // forward with checkpoints every S steps
+  for (long t = 0; t < K || t == 0; t += a->S) {
+    const long i = t / a->S;
+    if (i >= nck) break;
+    ACK(cudaMemcpyAsync(a->ckpt[i], c->f[c->cur], sb, cudaMemcpyDeviceToDevice, st), "store checkpoint");
+    const long len = std::min(a->S, K - t);
+    if (len > 0) {
+      const int rc = mrtlb_step(c, len);
+      if (rc) return rc;
+    }
+    if (K == 0) break;
+  }
+  return MRTLB_OK;
+}
+
+extern "C" int mrtlb_adjoint_backward(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK,
+                                      double dL_ds[16], double* dL_df0) {
+  if (!c) return MRTLB_ERR_ARG;
+  if (!c->adj) return afail(c, MRTLB_ERR_STATE, "call mrtlb_adjoint_forward first");
+  if (!dL_dmacros && !dL_dfK) return afail(c, MRTLB_ERR_ARG, "a seed (dL/dmacros or dL/df^K) is required");
+  const int rc = (c->prec == MRTLB_FP64) ? backward_impl<double>(c, dL_dmacros, dL_dfK, dL_ds, dL_df0)
+                                         : backward_impl<float>(c, dL_dmacros, dL_dfK, dL_ds, dL_df0);
+  return rc;
+}
+
+extern "C" int mrtlb_adjoint_release(mrtlb_ctx* c) {
+  if (!c) return MRTLB_ERR_ARG;
+  if (c->adj) cudaStreamSynchronize(c->stream);
+  release(c->adj);
+  c->adj = nullptr;
+  return MRTLB_OK;
+}
+
+extern "C" int mrtlb_equilibrium_adjoint(mrtlb_ctx* c, const double* dL_df, const double* rho,
+                                         const double* ux, const double* uy, const double* T,
+                                         double* dL_drho, double* dL_dux, double* dL_duy, double* dL_dT) {
+  if (!c || !dL_df || !rho || !ux || !uy || !T || !dL_drho || !dL_dux || !dL_duy || !dL_dT)
+    return MRTLB_ERR_ARG;
+  if (c->p.eq_version == 3)
+    return afail(c, MRTLB_ERR_UNSUPPORTED, "the adjoint covers equilibrium versions 1 and 2");
+  const long long n = (long long)c->L.nx * c->L.ny;
+  eq_adjoint_kernel<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(dL_df, rho, ux, uy, T, dL_drho, dL_dux,
+                                                                         dL_duy, dL_dT, n, c->c64);
+  ACK(cudaGetLastError(), "equilibrium adjoint");
+  ACK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return MRTLB_OK;
+}
+
+void mrtlb_adjoint_free_internal(mrtlb_ctx* c) {
+  if (c && c->adj) {
+    release(c->adj);
+    c->adj = nullptr;
+  }
+}

@@ -11,6 +11,8 @@
 
 using namespace mrtlb;
 
+struct mrtlb_adjoint_state;  // adjoint.cu
+
 struct mrtlb_ctx {
   mrtlb_params p{};
   double s[16]{};
@@ -38,5 +40,9 @@ struct mrtlb_ctx {
   cudaEvent_t* ev = nullptr;
   int ev_cap = 0, ev_used = 0;
   bool timing = false;
+  mrtlb_adjoint_state* adj = nullptr;  // checkpoints and buffers of the adjoint
   std::string last_error;
 };
+
+void mrtlb_adjoint_free_internal(mrtlb_ctx* c);
+

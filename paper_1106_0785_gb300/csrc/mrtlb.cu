@@ -529,6 +529,27 @@ extern "C" int mrtlb_set_f(mrtlb_ctx* c, const void* f, int on_device) {
 
 extern "C" long mrtlb_step_count(const mrtlb_ctx* c) { return c ? c->steps : -1; }
 
+extern "C" int mrtlb_set_rates(mrtlb_ctx* c, const double* s) {
+  if (!c || !s) return MRTLB_ERR_ARG;
+  for (int q = 4; q < 16; ++q)
+    if (!(s[q] >= 0) || s[q] * c->p.dt > 2.0)
+      return fail(c, MRTLB_ERR_ARG, "s_%d = %g: need 0 <= s dt <= 2", q + 1, s[q]);
+  if (c->p.modified && (!(s[4] > 0) || !(s[5] > 0)))
+    return fail(c, MRTLB_ERR_ARG, "the modified collision needs s5, s6 > 0");
+  if (c->f[0]) {
+    const cudaError_t e = cudaStreamSynchronize(c->stream);  // queued steps use the old rates
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  }
+  for (int q = 0; q < 16; ++q) c->s[q] = s[q];
+  return build_coefficients(c);
+}
+
+extern "C" int mrtlb_get_rates(const mrtlb_ctx* c, double* s) {
+  if (!c || !s) return MRTLB_ERR_ARG;
+  for (int q = 0; q < 16; ++q) s[q] = c->s[q];
+  return MRTLB_OK;
+}
+
 static void free_events(mrtlb_ctx* c) {
   for (int k = 0; k < 2 * c->ev_cap; ++k) cudaEventDestroy(c->ev[k]);
   delete[] c->ev;
@@ -596,5 +617,6 @@ extern "C" void mrtlb_destroy(mrtlb_ctx* c) {
   if (c->Tprev) cudaFree(c->Tprev);
   if (c->staging) cudaFree(c->staging);
   if (c->ev) free_events(c);
+  mrtlb_adjoint_free_internal(c);
   delete c;
 }

@@ -45,6 +45,8 @@ EXPORTS = (
     "mrtlb_batch_create", "mrtlb_batch_step", "mrtlb_batch_sync", "mrtlb_batch_set_tiles",
     "mrtlb_batch_get_tiles", "mrtlb_batch_set_graph_steps", "mrtlb_batch_tune", "mrtlb_batch_nodes",
     "mrtlb_batch_last_error", "mrtlb_batch_destroy",
+    "mrtlb_set_rates", "mrtlb_get_rates", "mrtlb_adjoint_forward", "mrtlb_adjoint_backward",
+    "mrtlb_adjoint_release", "mrtlb_equilibrium_adjoint",
 )
 
 MRTLB_NOALLOC_MAX_NODES = 1 << 20
@@ -127,6 +129,13 @@ def load(path=LIB_PATH):
     lib.mrtlb_batch_last_error.restype = ctypes.c_char_p
     lib.mrtlb_batch_destroy.argtypes = [P]
     lib.mrtlb_batch_destroy.restype = None
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.mrtlb_set_rates.argtypes = [P, D]
+    lib.mrtlb_get_rates.argtypes = [P, D]
+    lib.mrtlb_adjoint_forward.argtypes = [P, ctypes.c_long]
+    lib.mrtlb_adjoint_backward.argtypes = [P, P, P, D, P]
+    lib.mrtlb_adjoint_release.argtypes = [P]
+    lib.mrtlb_equilibrium_adjoint.argtypes = [P] + [P] * 9
     _lib = lib
     return lib
 
@@ -299,6 +308,40 @@ def mrtlb_batch_last_error(b):
 
 def mrtlb_batch_destroy(b):
     load().mrtlb_batch_destroy(b)
+
+
+def mrtlb_set_rates(ctx, s):
+    a = np.ascontiguousarray(np.asarray(s, dtype=np.float64))
+    assert a.shape == (16,)
+    _check(load().mrtlb_set_rates(ctx, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), ctx)
+
+
+def mrtlb_get_rates(ctx):
+    a = np.zeros(16)
+    _check(load().mrtlb_get_rates(ctx, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), ctx)
+    return a
+
+
+def mrtlb_adjoint_forward(ctx, K):
+    _check(load().mrtlb_adjoint_forward(ctx, int(K)), ctx)
+
+
+def mrtlb_adjoint_backward(ctx, dL_dmacros=None, dL_dfK=None, dL_df0=None):
+    """Device FP64 seeds in, (dL/ds numpy[16]) out; dL_df0 (device FP64) filled if given."""
+    ds = np.zeros(16)
+    _check(load().mrtlb_adjoint_backward(ctx, _ptr(dL_dmacros), _ptr(dL_dfK),
+                                         ds.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         _ptr(dL_df0)), ctx)
+    return ds
+
+
+def mrtlb_adjoint_release(ctx):
+    _check(load().mrtlb_adjoint_release(ctx), ctx)
+
+
+def mrtlb_equilibrium_adjoint(ctx, dL_df, rho, ux, uy, T, out_rho, out_ux, out_uy, out_T):
+    _check(load().mrtlb_equilibrium_adjoint(ctx, *[_ptr(a) for a in (dL_df, rho, ux, uy, T, out_rho, out_ux,
+                                                                      out_uy, out_T)]), ctx)
 
 
 def mrtlb_launches_per_step(ctx):

@@ -89,6 +89,35 @@ class Simulation:
     def steps(self):
         return M.mrtlb_step_count(self.ctx)
 
+    # -- rates and the adjoint ---------------------------------------------------
+    def set_rates(self, s):
+        M.mrtlb_set_rates(self.ctx, s)
+
+    def rates(self):
+        return M.mrtlb_get_rates(self.ctx)
+
+    def adjoint_forward(self, K):
+        """Advance K steps storing sqrt(K) checkpoints for adjoint_backward."""
+        M.mrtlb_adjoint_forward(self.ctx, K)
+
+    def adjoint_backward(self, dL_dmacros=None, dL_dfK=None, want_df0=True):
+        """Seeds: device FP64 [4][ny][nx] (rho, ux, uy, T) and/or [16][ny][nx].
+        Returns (dL/ds numpy[16], dL/df0 device FP64 [16][ny][nx] or None)."""
+        t = self.torch
+        conv = lambda a: None if a is None else a.to(self.device, t.float64).contiguous()
+        dm, df = conv(dL_dmacros), conv(dL_dfK)
+        out = t.empty((16, self.cfg.ny, self.cfg.nx), dtype=t.float64, device=self.device) if want_df0 else None
+        ds = M.mrtlb_adjoint_backward(self.ctx, dm, df, out)
+        return ds, out
+
+    def equilibrium_adjoint(self, dL_df, rho, ux, uy, T):
+        """dL/d(rho, ux, uy, T) of an equilibrium initial state (device FP64)."""
+        t = self.torch
+        ins = [a.to(self.device, t.float64).contiguous() for a in (dL_df, rho, ux, uy, T)]
+        outs = [t.empty((self.cfg.ny, self.cfg.nx), dtype=t.float64, device=self.device) for _ in range(4)]
+        M.mrtlb_equilibrium_adjoint(self.ctx, *ins, *outs)
+        return tuple(outs)
+
     def close(self):
         if self.ctx is not None:
             M.mrtlb_destroy(self.ctx)

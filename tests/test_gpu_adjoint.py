@@ -1,0 +1,154 @@
+"""The hand-written adjoint against the FP64 oracle's exact tangent.
+
+For random directions v (on the initial state) and w (on the final state),
+<w, J v> from a complex-step derivative of the oracle's steps must equal
+<J^T w, v> from the CUDA adjoint (FP64 path), and the rate gradients must
+equal <w, dF/ds_k> from complex steps in s_k.  These dot-product tests pin
+every term of the transpose: Lax-Wendroff, collision, the modification's
+local and neighbour terms, ghosts and NEE walls, and the checkpointed
+multi-step recompute.
+"""
+import numpy as np
+import pytest
+
+from oracle import equilibrium as oeq
+from oracle import fdlb
+from paper_1106_0785_gb300 import mrtlb as M
+from paper_1106_0785_gb300 import workloads
+from paper_1106_0785_gb300.simulation import Simulation
+
+pytestmark = pytest.mark.gpu
+
+H = 1e-30
+
+BCS = {
+    "periodic": (("periodic", 0, 0, 1),) * 4,
+    "outflow_x": (("outflow", 0, 0, 1),) * 2 + (("periodic", 0, 0, 1),) * 2,
+    "walls_y": (("periodic", 0, 0, 1),) * 2 + (("wall", 0.1, 0.0, 1.1), ("wall", 0.5, -0.05, 0.95)),
+    "walls_x": (("wall", 0.02, 0.3, 1.0), ("wall", 0.0, -0.2, 1.2)) + (("outflow", 0, 0, 1),) * 2,
+}
+
+
+def _cfg(nx, ny, bc, version=1, precision="fp64"):
+    s = np.random.default_rng(5).uniform(50, 2000, 16)
+    s[:4] = 0
+    return M.Config(nx=nx, ny=ny, dx=0.01, dy=0.011, dt=2e-4, s=tuple(s), bc=bc,
+                    eq_version=version, precision=precision)
+
+
+def _oracle_params(cfg, s=None):
+    sides = tuple(fdlb.Side({"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW, "wall": fdlb.WALL}[k], a, b, t)
+                  for k, a, b, t in cfg.bc)
+    p = fdlb.Params(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt, s=np.asarray(cfg.s),
+                    sides=sides, version=cfg.eq_version, modified=cfg.modified)
+    if s is not None:
+        p.s = s
+    return p
+
+
+def _state(cfg, seed):
+    rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, seed)
+    f0 = oeq.feq(rho, ux, uy, T, cfg.eq_version) + workloads.noise((16, cfg.ny, cfg.nx), seed + 1, 1e-3)
+    return fdlb.prepare(f0, _oracle_params(cfg))
+
+
+def _adjoint(cuda, cfg, f0, K, w=None, seed_macros=None):
+    import torch
+    with Simulation(cfg) as sim:
+        sim.set_f(f0)
+        sim.adjoint_forward(K)
+        dm = None if seed_macros is None else torch.from_numpy(seed_macros).to(cuda)
+        dw = None if w is None else torch.from_numpy(w).to(cuda)
+        ds, df0 = sim.adjoint_backward(dL_dmacros=dm, dL_dfK=dw)
+        return ds, df0.cpu().numpy()
+
+
+@pytest.mark.parametrize("bc", list(BCS))
+@pytest.mark.parametrize("version", [1, 2])
+def test_one_step_adjoint_dot_product(cuda, bc, version):
+    cfg = _cfg(140, 21, BCS[bc], version)
+    f0 = _state(cfg, 100)
+    rng = np.random.default_rng(101)
+    v = rng.standard_normal(f0.shape)
+    w = rng.standard_normal(f0.shape)
+    ds, lam0 = _adjoint(cuda, cfg, f0, 1, w=w)
+    p = _oracle_params(cfg)
+    Jv = fdlb.step(f0 + 1j * H * v, p).imag / H
+    lhs, rhs = float((w * Jv).sum()), float((lam0 * v).sum())
+    assert abs(lhs - rhs) < 1e-11 * np.abs(w * Jv).sum(), (lhs, rhs)
+    # rate gradients: <w, dF/ds_k>
+    for k in range(4, 16):
+        sk = np.asarray(cfg.s, dtype=complex)
+        sk[k] += 1j * H
+        dF = fdlb.step(f0.astype(complex), _oracle_params(cfg, sk)).imag / H
+        ref = float((w * dF).sum())
+        assert abs(ds[k] - ref) < 1e-10 * np.abs(w * dF).sum(), (k, ds[k], ref)
+    assert np.all(ds[:4] == 0)
+
+
+def test_multi_step_adjoint_through_checkpoints(cuda):
+    """K = 7: checkpoints every 3 steps, segments 3 + 3 + 1 recomputed."""
+    cfg = _cfg(70, 13, BCS["walls_y"])
+    f0 = _state(cfg, 110)
+    rng = np.random.default_rng(111)
+    v = rng.standard_normal(f0.shape)
+    w = rng.standard_normal(f0.shape)
+    ds, lam0 = _adjoint(cuda, cfg, f0, 7, w=w)
+    p = _oracle_params(cfg)
+    Jv = fdlb.run(f0 + 1j * H * v, p, 7).imag / H
+    lhs, rhs = float((w * Jv).sum()), float((lam0 * v).sum())
+    assert abs(lhs - rhs) < 1e-10 * np.abs(w * Jv).sum()
+    k = 6
+    sk = np.asarray(cfg.s, dtype=complex)
+    sk[k] += 1j * H
+    dF = fdlb.run(f0.astype(complex), _oracle_params(cfg, sk), 7).imag / H
+    assert abs(ds[k] - float((w * dF).sum())) < 1e-9 * np.abs(w * dF).sum()
+
+
+def test_macro_seed(cuda):
+    """L = sum(a rho + b ux + c uy + d T) of the final macroscopic fields."""
+    cfg = _cfg(66, 17, BCS["outflow_x"])
+    f0 = _state(cfg, 120)
+    rng = np.random.default_rng(121)
+    weights = rng.standard_normal((4, cfg.ny, cfg.nx))
+    v = rng.standard_normal(f0.shape)
+    ds, lam0 = _adjoint(cuda, cfg, f0, 4, seed_macros=weights)
+    p = _oracle_params(cfg)
+    fK = fdlb.run(f0 + 1j * H * v, p, 4)
+    dL = float(sum((weights[k] * m).sum() for k, m in enumerate(fdlb.macros(fK))).imag / H)
+    assert abs(dL - float((lam0 * v).sum())) < 1e-10 * np.abs(weights).sum()
+
+
+def test_equilibrium_adjoint(cuda):
+    import torch
+    cfg = _cfg(50, 9, BCS["periodic"], version=2)
+    rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 130)
+    rng = np.random.default_rng(131)
+    lam = rng.standard_normal((16, cfg.ny, cfg.nx))
+    d = [rng.standard_normal((cfg.ny, cfg.nx)) for _ in range(4)]
+    with Simulation(cfg) as sim:
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(cuda)
+        outs = sim.equilibrium_adjoint(t(lam), t(rho), t(ux), t(uy), t(T))
+    rhs = sum(float((o.cpu().numpy() * di).sum()) for o, di in zip(outs, d))
+    jf = oeq.feq(rho + 1j * H * d[0], ux + 1j * H * d[1], uy + 1j * H * d[2], T + 1j * H * d[3], 2).imag / H
+    lhs = float((lam * jf).sum())
+    assert abs(lhs - rhs) < 1e-11 * np.abs(lam * jf).sum()
+
+
+def test_fp32_adjoint_close_to_fp64(cuda):
+    cfg64 = _cfg(140, 21, BCS["walls_y"])
+    f0 = _state(cfg64, 140)
+    w = np.random.default_rng(141).standard_normal(f0.shape)
+    ds64, l64 = _adjoint(cuda, cfg64, f0, 5, w=w)
+    cfg32 = _cfg(140, 21, BCS["walls_y"], precision="fp32")
+    ds32, l32 = _adjoint(cuda, cfg32, f0.astype(np.float32), 5, w=w)
+    assert np.abs(l32 - l64).max() < 1e-4 * np.abs(l64).max()
+    assert np.allclose(ds32[4:], ds64[4:], rtol=1e-3, atol=1e-4 * np.abs(ds64).max())
+
+
+def test_adjoint_rejects_version_3(cuda):
+    cfg = _cfg(20, 5, BCS["periodic"], version=3)
+    with Simulation(cfg) as sim:
+        with pytest.raises(M.MrtlbError) as ei:
+            sim.adjoint_forward(2)
+        assert ei.value.code == M.MRTLB_ERR_UNSUPPORTED
