@@ -26,6 +26,7 @@ data-path collective); the max time over ranks is reported.
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import subprocess
@@ -53,6 +54,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--adjoint-steps", type=int, default=64)
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
@@ -336,6 +339,11 @@ def run_mine(args, world, rank, local):
            "d2h_bytes_per_step": int(sum(o.numel() for o in outs) * 8)}
     sim.close()
 
+    # ---- forward + adjoint (sqrt(K) checkpointing) on the same input ---------
+    fwd_adj = None
+    if not args.no_adjoint:
+        fwd_adj = run_fwd_adj(args, world, dev, cfg, fields, nodes)
+
     # ---- the all-FP64 path on the same input --------------------------------
     cfg64, _ = workloads.richtmyer_meshkov(nx=NX, ny=NY, precision="fp64")
     sim64 = Simulation(cfg64, device=dev)
@@ -375,11 +383,45 @@ def run_mine(args, world, rank, local):
         "fp64_mlups": fp64_mlups,
         "fp64_ms_per_step": ms64 / args.fp64_steps,
         "batched": batched,
+        "fwd_adj": fwd_adj,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
+
+
+def run_fwd_adj(args, world, dev, cfg, fields, nodes):
+    """K FP32 steps forward with sqrt(K) checkpoints, then the adjoint back to
+    the initial state (seed: dL/dT = 1 on every node).  MLUPS = nodes * K /
+    total time; algorithmic bytes 320 / node update (forward 128 + adjoint:
+    read f, read lambda, write lambda, 64 each)."""
+    import torch
+
+    from paper_1106_0785_gb300.simulation import Simulation
+
+    K = args.adjoint_steps
+    sim = Simulation(cfg, device=dev)
+    seed = torch.zeros((4, cfg.ny, cfg.nx), dtype=torch.float64, device=dev)
+    seed[3] = 1.0
+    sim.init_equilibrium(*fields)
+    sim.adjoint_forward(K)  # warm-up (allocations, graphs)
+    sim.adjoint_backward(dL_dmacros=seed, want_df0=False)
+    sim.init_equilibrium(*fields)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sim.adjoint_forward(K)
+    ds, _ = sim.adjoint_backward(dL_dmacros=seed, want_df0=False)
+    torch.cuda.synchronize(dev)
+    el = max_over_ranks(time.perf_counter() - t0, world, dev)
+    sim.close()
+    peak, _ = measured_peaks()
+    gbs = 320 * nodes * K / el / 1e9
+    return {"K": K, "checkpoint_every": int(math.ceil(math.sqrt(K))),
+            "mlups": world * nodes * K / el / 1e6, "seconds": el,
+            "algorithmic_gbs": gbs, "frac_of_hbm": gbs / peak,
+            "dL_ds_visc": float(ds[4] + ds[5]), "dL_ds_cond": float(ds[6] + ds[7])}
 
 
 def run_batched(args, world, dev):

@@ -40,6 +40,10 @@ struct mrtlb_ctx {
   cudaEvent_t* ev = nullptr;
   int ev_cap = 0, ev_used = 0;
   bool timing = false;
+  // time loop as CUDA graphs of graph_steps steps, one per starting parity
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_steps = 64;
   mrtlb_adjoint_state* adj = nullptr;  // checkpoints and buffers of the adjoint
   std::string last_error;
 };

@@ -106,6 +106,8 @@ static int fail(mrtlb_ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
+static void drop_graphs(mrtlb_ctx* c);
+
 static int cuda_fail(mrtlb_ctx* c, cudaError_t e, const char* what) {
   return fail(c, MRTLB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -351,17 +353,13 @@ extern "C" int mrtlb_bind(mrtlb_ctx* c, void* f_a, void* f_b, size_t bytes) {
   if (rc) return rc;
   CK(cudaMemsetAsync(f_a, 0, c->state_bytes, c->stream), "cudaMemsetAsync");
   CK(cudaMemsetAsync(f_b, 0, c->state_bytes, c->stream), "cudaMemsetAsync");
+  drop_graphs(c);
   rc = plan_tiled(c->L, (int)c->esize, c->f[0], c->f[1], &c->plan);
   if (rc) return fail(c, MRTLB_ERR_CUDA, "tensor-map set-up failed (%d)", rc);
   return MRTLB_OK;
 }
 
 static bool bound(mrtlb_ctx* c) { return c && c->f[0] && c->f[1]; }
-
-static void enqueue_walls(mrtlb_ctx* c, void* f) {
-  if (c->prec == MRTLB_FP64) launch_walls<double>((double*)f, c->L, c->c64, c->walls, c->stream);
-  else launch_walls<float>((float*)f, c->L, c->c64, c->walls, c->stream);
-}
 
 static void enqueue_bc(mrtlb_ctx* c, void* f) {
   if (c->prec == MRTLB_FP64) launch_bc<double>((double*)f, c->L, c->c64, c->walls, c->stream);
@@ -400,25 +398,71 @@ extern "C" int mrtlb_init_equilibrium(mrtlb_ctx* c, const double* rho, const dou
   return check_launch(c, "init_equilibrium");
 }
 
-static int enqueue_steps(mrtlb_ctx* c, long nsteps) {
+// one step reading buffer `cur` (walls refilled, then the step kernel)
+static void enqueue_one(mrtlb_ctx* c, int cur, cudaStream_t st, bool timed) {
   const bool tiled = use_tiled(c->kernel, c->plan, c->prec == MRTLB_FP64);
-  for (long n = 0; n < nsteps; ++n) {
-    void* fin = c->f[c->cur];
-    void* fout = c->f[c->cur ^ 1];
-    enqueue_walls(c, fin);  // ghosts of fin were written through by the previous step
-    const bool timed = c->timing && c->ev_used < c->ev_cap;
-    if (timed) cudaEventRecord(c->ev[2 * c->ev_used], c->stream);
-    if (c->prec == MRTLB_FP64) {
-      if (tiled) launch_step_tiled<double>(c->plan, c->cur, c->L, c->c64, c->err, c->stream, fout);
-      else launch_step_plain<double>((const double*)fin, (double*)fout, c->L, c->c64, c->err, c->stream);
-    } else {
-      if (tiled) launch_step_tiled<float>(c->plan, c->cur, c->L, c->c32, c->err, c->stream, fout);
-      else launch_step_plain<float>((const float*)fin, (float*)fout, c->L, c->c32, c->err, c->stream);
+  void* fin = c->f[cur];
+  void* fout = c->f[cur ^ 1];
+  // (ghosts of fin were written through by the previous step)
+  if (c->prec == MRTLB_FP64) launch_walls<double>((double*)fin, c->L, c->c64, c->walls, st);
+  else launch_walls<float>((float*)fin, c->L, c->c64, c->walls, st);
+  if (timed) cudaEventRecord(c->ev[2 * c->ev_used], st);
+  if (c->prec == MRTLB_FP64) {
+    if (tiled) launch_step_tiled<double>(c->plan, cur, c->L, c->c64, c->err, st, fout);
+    else launch_step_plain<double>((const double*)fin, (double*)fout, c->L, c->c64, c->err, st);
+  } else {
+    if (tiled) launch_step_tiled<float>(c->plan, cur, c->L, c->c32, c->err, st, fout);
+    else launch_step_plain<float>((const float*)fin, (float*)fout, c->L, c->c32, c->err, st);
+  }
+  if (timed) {
+    cudaEventRecord(c->ev[2 * c->ev_used + 1], st);
+    ++c->ev_used;
+  }
+}
+
+static void drop_graphs(mrtlb_ctx* c) {
+  for (int p = 0; p < 2; ++p)
+    if (c->graph[p]) {
+      cudaGraphExecDestroy(c->graph[p]);
+      c->graph[p] = nullptr;
     }
-    if (timed) {
-      cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream);
-      ++c->ev_used;
-    }
+}
+
+// capture graph_steps steps starting at parity p; false if capture is not possible
+static bool ensure_graph(mrtlb_ctx* c, int p) {
+  if (c->graph[p]) return true;
+  if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  int cur = p;
+  for (int k = 0; k < c->graph_steps; ++k) {
+    enqueue_one(c, cur, c->cap, false);
+    cur ^= 1;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(c->cap, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return false;
+  }
+  const bool ok = cudaGraphInstantiate(&c->graph[p], g, 0) == cudaSuccess;
+  cudaGraphDestroy(g);
+  if (!ok) {
+    c->graph[p] = nullptr;
+    cudaGetLastError();
+  }
+  return ok;
+}
+
+static int enqueue_steps(mrtlb_ctx* c, long nsteps) {
+  long n = 0;
+  // runs of graph_steps steps replay as CUDA graphs (not while timing kernels)
+  while (!c->timing && c->graph_steps > 0 && nsteps - n >= c->graph_steps && ensure_graph(c, c->cur)) {
+    const cudaError_t e = cudaGraphLaunch(c->graph[c->cur], c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+    n += c->graph_steps;
+    if (c->graph_steps & 1) c->cur ^= 1;
+  }
+  for (; n < nsteps; ++n) {
+    enqueue_one(c, c->cur, c->stream, c->timing && c->ev_used < c->ev_cap);
     c->cur ^= 1;
   }
   c->steps += nsteps;
@@ -541,6 +585,7 @@ extern "C" int mrtlb_set_rates(mrtlb_ctx* c, const double* s) {
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
   }
   for (int q = 0; q < 16; ++q) c->s[q] = s[q];
+  drop_graphs(c);  // captured launches hold the old coefficients
   return build_coefficients(c);
 }
 
@@ -601,6 +646,7 @@ extern "C" int mrtlb_set_kernel(mrtlb_ctx* c, int which) {
   if (which == MRTLB_KERNEL_TILED && !tiled_supported(c->plan))
     return fail(c, MRTLB_ERR_UNSUPPORTED, "the tiled kernel is not available for this grid/binding");
   c->kernel = which;
+  drop_graphs(c);
   return MRTLB_OK;
 }
 
@@ -617,6 +663,8 @@ extern "C" void mrtlb_destroy(mrtlb_ctx* c) {
   if (c->Tprev) cudaFree(c->Tprev);
   if (c->staging) cudaFree(c->staging);
   if (c->ev) free_events(c);
+  drop_graphs(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
   mrtlb_adjoint_free_internal(c);
   delete c;
 }

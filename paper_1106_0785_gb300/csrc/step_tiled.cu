@@ -141,7 +141,10 @@ bool use_tiled(int which, const TiledPlan& plan, bool fp64) {
   (void)fp64;
   if (!plan.ok) return false;
   if (which == MRTLB_KERNEL_PLAIN) return false;
-  return true;
+  if (which == MRTLB_KERNEL_TILED) return true;
+  // AUTO: a march of a few rows is latency-bound (each row waits for its
+  // copy); small grids go to the one-thread-per-node kernel
+  return plan.seglen >= 16;
 }
 
 template <typename R>
