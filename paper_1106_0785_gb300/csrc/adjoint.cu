@@ -37,7 +37,9 @@ template <typename R>
 struct AdjCoef {
   Coef<R> c;
   R dt;
-  R s5, s6, s7, s8;
+  // derivatives of the modification factors dt (s7/s5 - 1), ... :
+  // dt/s5, dt/s6, dt s7/s5^2, dt s7/s6^2, dt s8/s5^2, dt s8/s6^2
+  R g[6];
 };
 
 template <typename R>
@@ -51,26 +53,36 @@ __device__ __forceinline__ void load16(const R* f, long long plane, long long at
   for (int q = 0; q < 16; ++q) g[q] = f[q * plane + at];
 }
 
-// Pass 1: adjoints of the two strain combinations of the modification at
-// every advanced node r (zero elsewhere, from the buffer's initial clear).
+// Pass 1, every node of [-1, nx] x [-1, ny]: the velocity u = j / rho of
+// B(f) into two planes and, at advanced nodes, the adjoints of the two
+// strain combinations of the modification (zero elsewhere):
+//   gbar_shear  = dL/d(du_x/dx - du_y/dy),  gbar_strain = dL/d(du_y/dx + du_x/dy).
 template <typename R>
-__global__ void adj_gbar_kernel(const R* __restrict__ ft, const R* __restrict__ lam, R* gsh, R* gst,
-                                Layout L, AdjCoef<R> a) {
-  const int i = L.i0 + blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = L.j0 + blockIdx.y;
-  if (i >= L.i1 || j >= L.j1) return;
+__global__ void adj_prep_kernel(const R* __restrict__ ft, const R* __restrict__ lam, R* Ux, R* Uy, R* gsh,
+                                R* gst, Layout L, AdjCoef<R> a) {
+  const int i = -1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = -1 + (int)blockIdx.y;
+  if (i > L.nx || ((i < 0 || i >= L.nx) && (j < 0 || j >= L.ny))) return;
   const long long at = L.node(i, j);
-  R g[16], lb[16], cb[16];
+  R g[16];
   load16(ft, L.plane, at, g);
+  R rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const R ir = (rho > R(0)) ? R(1) / rho : R(0);
+  const R ux = jx * ir, uy = jy * ir;
+  Ux[at] = ux;
+  Uy[at] = uy;
+  if (!advanced<R>(L, i, j) || !a.c.modified) {
+    gsh[at] = R(0);
+    gst[at] = R(0);
+    return;
+  }
+  R lb[16], cb[16];
   load16(lam, L.plane, at, lb);
 #pragma unroll
   for (int q = 0; q < 16; ++q) lb[q] = -lb[q];  // dL/dC = -lambda
   inverse_T(a.c, lb, cb, false);
-  R rho, jx, jy, e;
-  conserved(g, rho, jx, jy, e);
-  const R ir = R(1) / rho;
-  const R ux = jx * ir, uy = jy * ir;
-  const R P = rho * temperature(rho, jx, jy, e, ir);
+  const R P = e - R(0.5) * (jx * ux + jy * uy);  // rho T
   gsh[at] = cb[6] * a.c.mod[0] * P * ux + cb[7] * a.c.mod[3] * P * uy;
   gst[at] = cb[6] * a.c.mod[1] * P * uy + cb[7] * a.c.mod[2] * P * ux;
 }
@@ -81,29 +93,19 @@ __device__ __forceinline__ R gbar_at(const R* gb, const Layout& L, int i, int j)
   return gb[L.node(i, j)];
 }
 
-template <typename R>
-__device__ __forceinline__ void velocity_at(const R* ft, const Layout& L, int i, int j, R& ux, R& uy) {
-  R g[16];
-  load16(ft, L.plane, L.node(i, j), g);
-  R rho, jx, jy, e;
-  conserved(g, rho, jx, jy, e);
-  const R ir = R(1) / rho;
-  ux = jx * ir;
-  uy = jy * ir;
-}
-
 // Pass 2: lambda~(p) for every node of [-1, nx] x [-1, ny] (corners excluded)
 // plus the rate gradients of the advanced nodes.
 template <typename R>
 __global__ void __launch_bounds__(128) adj_core_kernel(const R* __restrict__ ft, const R* __restrict__ lam,
+                                                       const R* __restrict__ Ux, const R* __restrict__ Uy,
                                                        const R* __restrict__ gsh, const R* __restrict__ gst,
                                                        R* __restrict__ out, Layout L, AdjCoef<R> a,
                                                        double* gacc) {
   const int i = -1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   const int j = -1 + (int)blockIdx.y;
-  double G[16];
+  R G[16];  // rate gradients of this node (summed per warp, then in FP64)
 #pragma unroll
-  for (int k = 0; k < 16; ++k) G[k] = 0.0;
+  for (int k = 0; k < 16; ++k) G[k] = R(0);
   const bool inside = i <= L.nx && j <= L.ny && !((i < 0 || i >= L.nx) && (j < 0 || j >= L.ny));
   if (inside) {
     const Coef<R>& c = a.c;
@@ -115,8 +117,8 @@ __global__ void __launch_bounds__(128) adj_core_kernel(const R* __restrict__ ft,
     conserved(g, rho, jx, jy, e);
     // (ghost rows behind walls are never read by an advanced node and may be empty)
     const R ir = (rho > R(0)) ? R(1) / rho : R(0);
-    const R ux = jx * ir, uy = jy * ir;
-    const R T = temperature(rho, jx, jy, e, ir);
+    const R ux = Ux[at], uy = Uy[at];
+    const R T = (e - R(0.5) * (jx * ux + jy * uy)) * ir;  // the linearisation point
 #pragma unroll
     for (int q = 0; q < 16; ++q) lt[q] = R(0);
     if (advanced<R>(L, i, j)) {
@@ -131,13 +133,9 @@ __global__ void __launch_bounds__(128) adj_core_kernel(const R* __restrict__ ft,
         lt[q] = w * lp[q];
       }
       // forward quantities of the collision at p
-      R uxE, uyE, uxW, uyW, uxN, uyN, uxS, uyS;
-      velocity_at(ft, L, i + 1, j, uxE, uyE);
-      velocity_at(ft, L, i - 1, j, uxW, uyW);
-      velocity_at(ft, L, i, j + 1, uxN, uyN);
-      velocity_at(ft, L, i, j - 1, uxS, uyS);
-      const R shear = (uxE - uxW) * c.inv2dx - (uyN - uyS) * c.inv2dy;
-      const R strain = (uyE - uyW) * c.inv2dx + (uxN - uxS) * c.inv2dy;
+      const long long aE = at + 1, aW = at - 1, aN = at + L.pitch, aS = at - L.pitch;
+      const R shear = (Ux[aE] - Ux[aW]) * c.inv2dx - (Uy[aN] - Uy[aS]) * c.inv2dy;
+      const R strain = (Uy[aE] - Uy[aW]) * c.inv2dx + (Ux[aN] - Ux[aS]) * c.inv2dy;
       Harm<R> h;
       harmonics(g, h);
       R m[16], eq[16];
@@ -180,17 +178,16 @@ __global__ void __launch_bounds__(128) adj_core_kernel(const R* __restrict__ ft,
       for (int q = 0; q < 16; ++q) lt[q] += fb[q];
       // rate gradients: d f1 / d s_k through dt s_k (m_k - eq_k) and the
       // modification factors dt (s7/s5 - 1), ... (dL/dC = -lambda)
-      const double dt = (double)a.dt;
+      const R dt = a.dt;
 #pragma unroll
-      for (int k = 4; k < 16; ++k) G[k] = dt * (double)cb[k] * ((double)m[k] - (double)eq[k]);
+      for (int k = 4; k < 16; ++k) G[k] = dt * cb[k] * (m[k] - eq[k]);
       if (c.modified) {
-        const double A0 = (double)Pp * ux * shear, A1 = (double)Pp * uy * strain;
-        const double A2 = (double)Pp * ux * strain, A3 = (double)Pp * uy * shear;
-        const double s5 = a.s5, s6 = a.s6, s7 = a.s7, s8 = a.s8;
-        G[6] += (double)cb[6] * dt * (A0 / s5 + A1 / s6);
-        G[7] += (double)cb[7] * dt * (A2 / s6 + A3 / s5);
-        G[4] -= dt * ((double)cb[6] * A0 * s7 / (s5 * s5) + (double)cb[7] * A3 * s8 / (s5 * s5));
-        G[5] -= dt * ((double)cb[6] * A1 * s7 / (s6 * s6) + (double)cb[7] * A2 * s8 / (s6 * s6));
+        const R A0 = Pp * ux * shear, A1 = Pp * uy * strain;
+        const R A2 = Pp * ux * strain, A3 = Pp * uy * shear;
+        G[6] += cb[6] * (A0 * a.g[0] + A1 * a.g[1]);   // dt/s5, dt/s6
+        G[7] += cb[7] * (A2 * a.g[1] + A3 * a.g[0]);
+        G[4] -= cb[6] * A0 * a.g[2] + cb[7] * A3 * a.g[4];  // dt s7/s5^2, dt s8/s5^2
+        G[5] -= cb[6] * A1 * a.g[3] + cb[7] * A2 * a.g[5];  // dt s7/s6^2, dt s8/s6^2
       }
     }
     // (a) neighbours' Lax-Wendroff weights on p
@@ -219,13 +216,13 @@ __global__ void __launch_bounds__(128) adj_core_kernel(const R* __restrict__ ft,
 #pragma unroll
     for (int q = 0; q < 16; ++q) out[q * P + at] = lt[q];
   }
-  // block reduction of the rate gradients, one atomic per warp
+  // warp sums of the rate gradients, one FP64 atomic per warp and rate
 #pragma unroll
   for (int k = 4; k < 16; ++k) {
-    double v = G[k];
+    R v = G[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(gacc + k, v);
+    if ((threadIdx.x & 31) == 0 && v != R(0)) atomicAdd(gacc + k, (double)v);
   }
 }
 
@@ -396,6 +393,8 @@ struct mrtlb_adjoint_state {
   void* lam[2] = {nullptr, nullptr};
   void* gsh = nullptr;       // one padded plane each
   void* gst = nullptr;
+  void* ux = nullptr;
+  void* uy = nullptr;
   double* gacc = nullptr;
 };
 
@@ -419,7 +418,8 @@ void release(mrtlb_adjoint_state* a) {
   if (!a) return;
   for (void* p : a->ckpt) cudaFree(p);
   a->ckpt.clear();
-  for (void* p : {a->seg, a->work[0], a->work[1], a->lam[0], a->lam[1], a->gsh, a->gst, (void*)a->gacc})
+  for (void* p : {a->seg, a->work[0], a->work[1], a->lam[0], a->lam[1], a->gsh, a->gst, a->ux, a->uy,
+                  (void*)a->gacc})
     if (p) cudaFree(p);
   delete a;
 }
@@ -428,11 +428,14 @@ template <typename R>
 AdjCoef<R> adj_coef(const mrtlb_ctx* c, const Coef<R>& k) {
   AdjCoef<R> a;
   a.c = k;
-  a.dt = (R)c->p.dt;
-  a.s5 = (R)c->s[4];
-  a.s6 = (R)c->s[5];
-  a.s7 = (R)c->s[6];
-  a.s8 = (R)c->s[7];
+  const double dt = c->p.dt, s5 = c->s[4], s6 = c->s[5], s7 = c->s[6], s8 = c->s[7];
+  a.dt = (R)dt;
+  a.g[0] = (R)(dt / s5);
+  a.g[1] = (R)(dt / s6);
+  a.g[2] = (R)(dt * s7 / (s5 * s5));
+  a.g[3] = (R)(dt * s7 / (s6 * s6));
+  a.g[4] = (R)(dt * s8 / (s5 * s5));
+  a.g[5] = (R)(dt * s8 / (s6 * s6));
   return a;
 }
 
@@ -442,17 +445,10 @@ void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, const R* ft, const R* la
                   const Coef<R>& k, cudaStream_t st) {
   const Layout& L = c->L;
   const AdjCoef<R> ac = adj_coef<R>(c, k);
-  const size_t plane_bytes = (size_t)L.plane * sizeof(R);
-  cudaMemsetAsync(a->gsh, 0, plane_bytes, st);
-  cudaMemsetAsync(a->gst, 0, plane_bytes, st);
-  const int ni = L.i1 - L.i0, nj = L.j1 - L.j0;
-  if (ni > 0 && nj > 0) {
-    dim3 g1((ni + 127) / 128, nj);
-    adj_gbar_kernel<R><<<g1, 128, 0, st>>>(ft, lam_in, (R*)a->gsh, (R*)a->gst, L, ac);
-  }
   dim3 g2((L.nx + 2 + 127) / 128, L.ny + 2);
-  adj_core_kernel<R><<<g2, 128, 0, st>>>(ft, lam_in, (const R*)a->gsh, (const R*)a->gst, lam_out, L, ac,
-                                         a->gacc);
+  adj_prep_kernel<R><<<g2, 128, 0, st>>>(ft, lam_in, (R*)a->ux, (R*)a->uy, (R*)a->gsh, (R*)a->gst, L, ac);
+  adj_core_kernel<R><<<g2, 128, 0, st>>>(ft, lam_in, (const R*)a->ux, (const R*)a->uy, (const R*)a->gsh,
+                                         (const R*)a->gst, lam_out, L, ac, a->gacc);
   const int perim = 2 * L.nx + 2 * L.ny;
   adj_ghosts_kernel<R><<<(perim + 127) / 128, 128, 0, st>>>(lam_out, L);
   dim3 g3((std::max(L.nx, L.ny + 2) + 255) / 256, 16);
@@ -573,6 +569,9 @@ extern "C" int mrtlb_adjoint_forward(mrtlb_ctx* c, long K) {
   const size_t pb = (size_t)c->L.plane * c->esize;
   ACK(cudaMalloc(&a->gsh, pb), "cudaMalloc(gbar)");
   ACK(cudaMalloc(&a->gst, pb), "cudaMalloc(gbar)");
+  ACK(cudaMalloc(&a->ux, pb), "cudaMalloc(u)");
+  ACK(cudaMalloc(&a->uy, pb), "cudaMalloc(u)");
+  for (void* q : {a->gsh, a->gst, a->ux, a->uy}) ACK(cudaMemsetAsync(q, 0, pb, st), "clear");
   ACK(cudaMalloc((void**)&a->gacc, 16 * sizeof(double)), "cudaMalloc(grad)");
   plan_tiled(c->L, (int)c->esize, a->work[0], a->work[1], &a->plan);
   // forward with checkpoints every S steps
