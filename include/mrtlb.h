@@ -246,15 +246,25 @@ int mrtlb_get_rates(const mrtlb_ctx* ctx, double* s);
  * and the relaxation rates.  Equilibrium versions 1 and 2.
  *
  * mrtlb_adjoint_forward(ctx, K): advances the context K steps from its
- *   current state f^0 (like mrtlb_step) and stores a checkpoint every
- *   S = ceil(sqrt(K)) steps (library-owned device memory: about
- *   (K/S + S + 4) state buffers, freed by mrtlb_adjoint_release or destroy).
+ *   current state f^0 (like mrtlb_step) and keeps what the backward pass
+ *   needs in segments of S steps: the S states of the last segment, plus a
+ *   checkpoint at the start of every segment when there is more than one.
+ *   S is the value set by mrtlb_adjoint_set_interval, else K (no
+ *   recomputation) when K + 2 states fit in half the free device memory,
+ *   else ceil(sqrt(K)).  Library-owned device memory: S + 2 state buffers,
+ *   plus ceil(K/S) checkpoints when K > S; freed by mrtlb_adjoint_release or
+ *   destroy.
+ * mrtlb_adjoint_set_interval(ctx, S): the segment length of later
+ *   mrtlb_adjoint_forward calls; S = 0 restores the automatic choice,
+ *   S < 0 is MRTLB_ERR_ARG.  Memory against recomputation: each segment but
+ *   the last is recomputed once per backward pass.
  * mrtlb_adjoint_backward(ctx, dL_dmacros, dL_dfK, dL_ds, dL_df0): seeds
  *   with dL/d(rho, u_x, u_y, T) of the final state as mrtlb_macros returns it
  *   (device FP64 [4][ny][nx], or NULL) and/or dL/df^K of the state as
  *   mrtlb_get_f returns it (device FP64 [16][ny][nx], or NULL); recomputes
- *   each segment from its checkpoint on separate buffers (the context keeps
- *   f^K) and runs the adjoint steps back to f^0.  Outputs: dL_ds[16] (host;
+ *   each segment whose states are not held from its checkpoint (the context
+ *   keeps f^K) and runs the adjoint steps back to f^0.  It may be called
+ *   again with another seed after the same forward pass.  Outputs: dL_ds[16] (host;
  *   entries 5..16 of the paper's s, 0-based 4..15, accumulated in FP64;
  *   0..3 are zero since those rates have no effect) and dL/df^0 (device FP64
  *   [16][ny][nx], or NULL).  Synchronises.
@@ -263,6 +273,7 @@ int mrtlb_get_rates(const mrtlb_ctx* ctx, double* s);
  *   maps dL/df (device FP64 [16][ny][nx]) to dL/d(rho, u_x, u_y, T)
  *   (device FP64 [ny][nx] each).  Synchronises. */
 int mrtlb_adjoint_forward(mrtlb_ctx* ctx, long K);
+int mrtlb_adjoint_set_interval(mrtlb_ctx* ctx, long S);
 int mrtlb_adjoint_backward(mrtlb_ctx* ctx, const double* dL_dmacros, const double* dL_dfK,
                            double dL_ds[16], double* dL_df0);
 int mrtlb_adjoint_release(mrtlb_ctx* ctx);

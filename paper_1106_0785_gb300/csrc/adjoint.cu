@@ -93,21 +93,15 @@ __device__ __forceinline__ R gbar_at(const R* gb, const Layout& L, int i, int j)
   return gb[L.node(i, j)];
 }
 
-// Pass 2: lambda~(p) for every node of [-1, nx] x [-1, ny] (corners excluded)
-// plus the rate gradients of the advanced nodes.
+// Pass 2: lambda~(p) for one node p of [-1, nx] x [-1, ny] (corners
+// excluded); the rate gradients of an advanced node are added to G.
 template <typename R>
-__global__ void __launch_bounds__(128) adj_core_kernel(const R* __restrict__ ft, const R* __restrict__ lam,
-                                                       const R* __restrict__ Ux, const R* __restrict__ Uy,
-                                                       const R* __restrict__ gsh, const R* __restrict__ gst,
-                                                       R* __restrict__ out, Layout L, AdjCoef<R> a,
-                                                       double* gacc) {
-  const int i = -1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int j = -1 + (int)blockIdx.y;
-  R G[16];  // rate gradients of this node (summed per warp, then in FP64)
-#pragma unroll
-  for (int k = 0; k < 16; ++k) G[k] = R(0);
-  const bool inside = i <= L.nx && j <= L.ny && !((i < 0 || i >= L.nx) && (j < 0 || j >= L.ny));
-  if (inside) {
+__device__ __forceinline__ void adj_core_node(const R* __restrict__ ft, const R* __restrict__ lam,
+                                              const R* __restrict__ Ux, const R* __restrict__ Uy,
+                                              const R* __restrict__ gsh, const R* __restrict__ gst,
+                                              R* __restrict__ out, const Layout& L, const AdjCoef<R>& a, int i,
+                                              int j, R G[16]) {
+  {
     const Coef<R>& c = a.c;
     const long long P = L.plane;
     const long long at = L.node(i, j);
@@ -180,7 +174,7 @@ __global__ void __launch_bounds__(128) adj_core_kernel(const R* __restrict__ ft,
       // modification factors dt (s7/s5 - 1), ... (dL/dC = -lambda)
       const R dt = a.dt;
 #pragma unroll
-      for (int k = 4; k < 16; ++k) G[k] = dt * cb[k] * (m[k] - eq[k]);
+      for (int k = 4; k < 16; ++k) G[k] += dt * cb[k] * (m[k] - eq[k]);
       if (c.modified) {
         const R A0 = Pp * ux * shear, A1 = Pp * uy * strain;
         const R A2 = Pp * ux * strain, A3 = Pp * uy * shear;
@@ -215,6 +209,29 @@ __global__ void __launch_bounds__(128) adj_core_kernel(const R* __restrict__ ft,
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) out[q * P + at] = lt[q];
+  }
+}
+
+#ifndef MRTLB_ADJ_MINB
+#define MRTLB_ADJ_MINB 5
+#endif
+
+// Persistent over row tiles of 128 nodes (tile t: row -1 + t / tiles_x);
+// each thread sums the rate gradients of all its nodes before the warp
+// reduction.
+template <typename R>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? MRTLB_ADJ_MINB : 2)
+    adj_core_kernel(const R* __restrict__ ft, const R* __restrict__ lam, const R* __restrict__ Ux,
+                    const R* __restrict__ Uy, const R* __restrict__ gsh, const R* __restrict__ gst,
+                    R* __restrict__ out, Layout L, AdjCoef<R> a, double* gacc, int tiles_x, int ntiles) {
+  R G[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) G[k] = R(0);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int i = -1 + (t % tiles_x) * 128 + (int)threadIdx.x;
+    const int j = -1 + t / tiles_x;
+    if (i <= L.nx && !((i < 0 || i >= L.nx) && (j < 0 || j >= L.ny)))
+      adj_core_node(ft, lam, Ux, Uy, gsh, gst, out, L, a, i, j, G);
   }
   // warp sums of the rate gradients, one FP64 atomic per warp and rate
 #pragma unroll
@@ -385,20 +402,36 @@ __global__ void eq_adjoint_kernel(const double* __restrict__ lamd, const double*
 // host side
 // ---------------------------------------------------------------------------
 struct mrtlb_adjoint_state {
-  long K = 0, S = 0;
-  std::vector<void*> ckpt;   // states at t = 0, S, 2S, ... (padded)
-  void* seg = nullptr;       // S states of the segment being reversed
-  void* work[2] = {nullptr, nullptr};
-  TiledPlan plan{};
+  long K = 0, S = 0, nseg = 0;
+  std::vector<void*> ckpt;   // f^{sS} of every segment s (only when nseg > 1)
+  void* seg = nullptr;       // S slots: the states B(f^t) of one segment
+  long held = -1;            // the segment whose states the slots hold
+  std::vector<TiledPlan> plan;  // per slot: tensor map reading that slot
+  bool tiled = false;
   void* lam[2] = {nullptr, nullptr};
   void* gsh = nullptr;       // one padded plane each
   void* gst = nullptr;
   void* ux = nullptr;
   void* uy = nullptr;
   double* gacc = nullptr;
+  int core_blocks = 1;       // resident blocks of the core kernel on the device
 };
 
 namespace {
+
+// Blocks of the core kernel that fit on the device at once (its persistent grid).
+template <typename R>
+int core_resident_blocks() {
+#if defined(MRTLB_ADJ_PERSIST) && MRTLB_ADJ_PERSIST == 0
+  return 1 << 30;
+#else
+  int dev = 0, nsm = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj_core_kernel<R>, 128, 0);
+  return std::max(1, nsm) * std::max(1, per);
+#endif
+}
 
 int afail(mrtlb_ctx* c, int code, const char* msg) {
   c->last_error = msg;
@@ -418,8 +451,7 @@ void release(mrtlb_adjoint_state* a) {
   if (!a) return;
   for (void* p : a->ckpt) cudaFree(p);
   a->ckpt.clear();
-  for (void* p : {a->seg, a->work[0], a->work[1], a->lam[0], a->lam[1], a->gsh, a->gst, a->ux, a->uy,
-                  (void*)a->gacc})
+  for (void* p : {a->seg, a->lam[0], a->lam[1], a->gsh, a->gst, a->ux, a->uy, (void*)a->gacc})
     if (p) cudaFree(p);
   delete a;
 }
@@ -447,8 +479,10 @@ void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, const R* ft, const R* la
   const AdjCoef<R> ac = adj_coef<R>(c, k);
   dim3 g2((L.nx + 2 + 127) / 128, L.ny + 2);
   adj_prep_kernel<R><<<g2, 128, 0, st>>>(ft, lam_in, (R*)a->ux, (R*)a->uy, (R*)a->gsh, (R*)a->gst, L, ac);
-  adj_core_kernel<R><<<g2, 128, 0, st>>>(ft, lam_in, (const R*)a->ux, (const R*)a->uy, (const R*)a->gsh,
-                                         (const R*)a->gst, lam_out, L, ac, a->gacc);
+  const int ntiles = (int)(g2.x * g2.y);
+  const int grid = std::min(ntiles, a->core_blocks);
+  adj_core_kernel<R><<<grid, 128, 0, st>>>(ft, lam_in, (const R*)a->ux, (const R*)a->uy, (const R*)a->gsh,
+                                           (const R*)a->gst, lam_out, L, ac, a->gacc, (int)g2.x, ntiles);
   const int perim = 2 * L.nx + 2 * L.ny;
   adj_ghosts_kernel<R><<<(perim + 127) / 128, 128, 0, st>>>(lam_out, L);
   dim3 g3((std::max(L.nx, L.ny + 2) + 255) / 256, 16);
@@ -461,17 +495,29 @@ void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, const R* ft, const R* la
 }
 
 template <typename R>
-void walls_only(mrtlb_ctx* c, R* f, cudaStream_t st) {
-  launch_walls<R>(f, c->L, c->c64, c->walls, st);
+R* slot(const mrtlb_ctx* c, const mrtlb_adjoint_state* a, long n) {
+  return (R*)((char*)a->seg + (size_t)n * c->state_bytes);
+}
+
+// Run the states of segment sg (t0 = sg S, len steps) through the slots:
+// slot n becomes B(f^{t0+n}) (walls refilled, ghosts written through by the
+// step that produced it).  Slot 0 must hold f^{t0}.  The last step writes
+// into `last` unless it is null (then the segment's final state is not kept).
+template <typename R>
+void run_segment(mrtlb_ctx* c, mrtlb_adjoint_state* a, long len, const Coef<R>& k, cudaStream_t st, R* last) {
+  for (long n = 0; n < len; ++n) {
+    R* fin = slot<R>(c, a, n);
+    launch_walls<R>(fin, c->L, c->c64, c->walls, st);
+    R* fout = (n + 1 < len) ? slot<R>(c, a, n + 1) : last;
+    if (!fout) break;
+    if (a->tiled) launch_step_tiled<R>(a->plan[n], 0, c->L, k, c->err, st, fout);
+    else launch_step_plain<R>(fin, fout, c->L, k, c->err, st);
+  }
 }
 
 template <typename R>
-void step_on(mrtlb_ctx* c, mrtlb_adjoint_state* a, int cur, const Coef<R>& k, cudaStream_t st) {
-  R* fin = (R*)a->work[cur];
-  R* fout = (R*)a->work[cur ^ 1];
-  walls_only<R>(c, fin, st);
-  if (a->plan.ok) launch_step_tiled<R>(a->plan, cur, c->L, k, c->err, st, fout);
-  else launch_step_plain<R>(fin, fout, c->L, k, c->err, st);
+const Coef<R>& coef_of(const mrtlb_ctx* c) {
+  return *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&c->c32 : (const void*)&c->c64);
 }
 
 template <typename R>
@@ -480,7 +526,7 @@ int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, 
   mrtlb_adjoint_state* a = c->adj;
   const Layout& L = c->L;
   cudaStream_t st = c->stream;
-  const Coef<R>& k = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&c->c32 : (const void*)&c->c64);
+  const Coef<R>& k = coef_of<R>(c);
   const size_t sb = c->state_bytes;
   R* lam0 = (R*)a->lam[0];
   R* lam1 = (R*)a->lam[1];
@@ -506,40 +552,104 @@ int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, 
   R* lin = lam0;
   R* lout = lam1;
   const long K = a->K, S = a->S;
-  const long nseg = (K + S - 1) / S;
-  for (long sgi = nseg - 1; sgi >= 0; --sgi) {
+  for (long sgi = a->nseg - 1; sgi >= 0; --sgi) {
     const long t0 = sgi * S;
     const long len = std::min(S, K - t0);
-    // recompute the segment's states B(f^{t0}), ..., B(f^{t0+len-1})
-    ACK(cudaMemcpyAsync(a->work[0], a->ckpt[sgi], sb, cudaMemcpyDeviceToDevice, st), "restore checkpoint");
-    int cur = 0;
-    for (long n = 0; n < len; ++n) {
-      walls_only<R>(c, (R*)a->work[cur], st);
-      ACK(cudaMemcpyAsync((char*)a->seg + (size_t)n * sb, a->work[cur], sb, cudaMemcpyDeviceToDevice, st),
-          "store segment state");
-      if (n + 1 < len) {
-        step_on<R>(c, a, cur, k, st);
-        cur ^= 1;
-      }
+    if (a->held != sgi) {  // recompute the segment's states from its checkpoint
+      ACK(cudaMemcpyAsync(a->seg, a->ckpt[sgi], sb, cudaMemcpyDeviceToDevice, st), "restore checkpoint");
+      run_segment<R>(c, a, len, k, st, nullptr);
+      a->held = sgi;
     }
     for (long n = len - 1; n >= 0; --n) {
-      const R* ft = (const R*)((char*)a->seg + (size_t)n * sb);
-      adjoint_step<R>(c, a, ft, lin, lout, k, st);
+      adjoint_step<R>(c, a, slot<R>(c, a, n), lin, lout, k, st);
       std::swap(lin, lout);
-      ACK(cudaMemsetAsync(lout, 0, sb, st), "clear");
     }
   }
   ACK(cudaGetLastError(), "adjoint steps");
   if (dL_df0) {
     dim3 gd((L.nx + 127) / 128, L.ny, 16);
-      adj_dense_kernel<R><<<gd, 128, 0, st>>>(lin, dL_df0, L, 1);
+    adj_dense_kernel<R><<<gd, 128, 0, st>>>(lin, dL_df0, L, 1);
   }
   if (dL_ds) ACK(cudaMemcpyAsync(dL_ds, a->gacc, 16 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy grads");
   ACK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   return MRTLB_OK;
 }
 
+template <typename R>
+int forward_impl(mrtlb_ctx* c, long K) {
+  mrtlb_adjoint_state* a = c->adj;
+  const size_t sb = c->state_bytes;
+  cudaStream_t st = c->stream;
+  const bool fp64 = sizeof(R) == 8;
+  // segment length: every state when K + 2 states fit in half the free memory
+  long S = c->adj_interval;
+  if (S <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    S = ((size_t)(K + 2) * sb <= fr / 2) ? K : (long)std::ceil(std::sqrt((double)K));
+  }
+  a->K = K;
+  a->S = S = std::max(1L, std::min(S, std::max(K, 1L)));
+  a->nseg = std::max(1L, (K + S - 1) / S);
+  if (a->nseg > 1)
+    for (long i = 0; i < a->nseg; ++i) {
+      void* p = nullptr;
+      ACK(cudaMalloc(&p, sb), "cudaMalloc(checkpoint)");
+      a->ckpt.push_back(p);
+    }
+  ACK(cudaMalloc(&a->seg, sb * (size_t)S), "cudaMalloc(segment)");
+  for (int b = 0; b < 2; ++b) ACK(cudaMalloc(&a->lam[b], sb), "cudaMalloc(lambda)");
+  const size_t pb = (size_t)c->L.plane * c->esize;
+  ACK(cudaMalloc(&a->gsh, pb), "cudaMalloc(gbar)");
+  ACK(cudaMalloc(&a->gst, pb), "cudaMalloc(gbar)");
+  ACK(cudaMalloc(&a->ux, pb), "cudaMalloc(u)");
+  ACK(cudaMalloc(&a->uy, pb), "cudaMalloc(u)");
+  for (void* q : {a->gsh, a->gst, a->ux, a->uy}) ACK(cudaMemsetAsync(q, 0, pb, st), "clear");
+  ACK(cudaMalloc((void**)&a->gacc, 16 * sizeof(double)), "cudaMalloc(grad)");
+  a->core_blocks = core_resident_blocks<R>();
+  // one read map per slot for the tiled step (the write side is a plain pointer)
+  TiledPlan p0;
+  plan_tiled(c->L, (int)c->esize, a->seg, a->seg, &p0);
+  a->tiled = use_tiled(c->kernel, p0, fp64);
+  if (a->tiled) {
+    a->plan.resize(S);
+    for (long n = 0; n < S; ++n) {
+      void* sp = slot<R>(c, a, n);
+      if (plan_tiled(c->L, (int)c->esize, sp, sp, &a->plan[n]) != 0) {
+        a->tiled = false;
+        break;
+      }
+    }
+  }
+  // all segments but the last: checkpoint, then the context's own time loop
+  for (long sg = 0; sg + 1 < a->nseg; ++sg) {
+    ACK(cudaMemcpyAsync(a->ckpt[sg], c->f[c->cur], sb, cudaMemcpyDeviceToDevice, st), "store checkpoint");
+    const int rc = mrtlb_step(c, S);
+    if (rc) return rc;
+  }
+  // the last segment runs through the slots and stays there for the backward pass
+  const long t0 = (a->nseg - 1) * S, len = K - t0;
+  if (a->nseg > 1)
+    ACK(cudaMemcpyAsync(a->ckpt[a->nseg - 1], c->f[c->cur], sb, cudaMemcpyDeviceToDevice, st), "store checkpoint");
+  ACK(cudaMemcpyAsync(a->seg, c->f[c->cur], sb, cudaMemcpyDeviceToDevice, st), "copy state");
+  if (len > 0) {
+    run_segment<R>(c, a, len, coef_of<R>(c), st, (R*)c->f[c->cur ^ 1]);
+    c->cur ^= 1;
+    c->steps += len;
+  }
+  a->held = a->nseg - 1;
+  ACK(cudaGetLastError(), "adjoint forward");
+  return MRTLB_OK;
+}
+
 }  // namespace
+
+extern "C" int mrtlb_adjoint_set_interval(mrtlb_ctx* c, long S) {
+  if (!c) return MRTLB_ERR_ARG;
+  if (S < 0) return afail(c, MRTLB_ERR_ARG, "S < 0");
+  c->adj_interval = S;
+  return MRTLB_OK;
+}
 
 extern "C" int mrtlb_adjoint_forward(mrtlb_ctx* c, long K) {
   if (!c) return MRTLB_ERR_ARG;
@@ -549,44 +659,7 @@ extern "C" int mrtlb_adjoint_forward(mrtlb_ctx* c, long K) {
     return afail(c, MRTLB_ERR_UNSUPPORTED, "the adjoint covers equilibrium versions 1 and 2");
   release(c->adj);
   c->adj = new mrtlb_adjoint_state();
-  mrtlb_adjoint_state* a = c->adj;
-  a->K = K;
-  a->S = std::max(1L, (long)std::ceil(std::sqrt((double)std::max(K, 1L))));
-  const size_t sb = c->state_bytes;
-  const long nck = std::max(1L, (K + a->S - 1) / a->S);
-  cudaStream_t st = c->stream;
-  for (long i = 0; i < nck; ++i) {
-    void* p = nullptr;
-    ACK(cudaMalloc(&p, sb), "cudaMalloc(checkpoint)");
-    a->ckpt.push_back(p);
-  }
-  ACK(cudaMalloc(&a->seg, sb * (size_t)a->S), "cudaMalloc(segment)");
-  for (int b = 0; b < 2; ++b) {
-    ACK(cudaMalloc(&a->work[b], sb), "cudaMalloc(work)");
-    ACK(cudaMemsetAsync(a->work[b], 0, sb, st), "clear");
-    ACK(cudaMalloc(&a->lam[b], sb), "cudaMalloc(lambda)");
-  }
-  const size_t pb = (size_t)c->L.plane * c->esize;
-  ACK(cudaMalloc(&a->gsh, pb), "cudaMalloc(gbar)");
-  ACK(cudaMalloc(&a->gst, pb), "cudaMalloc(gbar)");
-  ACK(cudaMalloc(&a->ux, pb), "cudaMalloc(u)");
-  ACK(cudaMalloc(&a->uy, pb), "cudaMalloc(u)");
-  for (void* q : {a->gsh, a->gst, a->ux, a->uy}) ACK(cudaMemsetAsync(q, 0, pb, st), "clear");
-  ACK(cudaMalloc((void**)&a->gacc, 16 * sizeof(double)), "cudaMalloc(grad)");
-  plan_tiled(c->L, (int)c->esize, a->work[0], a->work[1], &a->plan);
-  // forward with checkpoints every S steps
-  for (long t = 0; t < K || t == 0; t += a->S) {
-    const long i = t / a->S;
-    if (i >= nck) break;
-    ACK(cudaMemcpyAsync(a->ckpt[i], c->f[c->cur], sb, cudaMemcpyDeviceToDevice, st), "store checkpoint");
-    const long len = std::min(a->S, K - t);
-    if (len > 0) {
-      const int rc = mrtlb_step(c, len);
-      if (rc) return rc;
-    }
-    if (K == 0) break;
-  }
-  return MRTLB_OK;
+  return (c->prec == MRTLB_FP64) ? forward_impl<double>(c, K) : forward_impl<float>(c, K);
 }
 
 extern "C" int mrtlb_adjoint_backward(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK,

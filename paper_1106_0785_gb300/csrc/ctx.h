@@ -45,6 +45,7 @@ struct mrtlb_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_steps = 64;
   mrtlb_adjoint_state* adj = nullptr;  // checkpoints and buffers of the adjoint
+  long adj_interval = 0;               // adjoint segment length (0: automatic)
   std::string last_error;
 };
 

@@ -45,7 +45,7 @@ EXPORTS = (
     "mrtlb_batch_create", "mrtlb_batch_step", "mrtlb_batch_sync", "mrtlb_batch_set_tiles",
     "mrtlb_batch_get_tiles", "mrtlb_batch_set_graph_steps", "mrtlb_batch_tune", "mrtlb_batch_nodes",
     "mrtlb_batch_last_error", "mrtlb_batch_destroy",
-    "mrtlb_set_rates", "mrtlb_get_rates", "mrtlb_adjoint_forward", "mrtlb_adjoint_backward",
+    "mrtlb_set_rates", "mrtlb_get_rates", "mrtlb_adjoint_forward", "mrtlb_adjoint_set_interval", "mrtlb_adjoint_backward",
     "mrtlb_adjoint_release", "mrtlb_equilibrium_adjoint",
 )
 
@@ -133,6 +133,7 @@ def load(path=LIB_PATH):
     lib.mrtlb_set_rates.argtypes = [P, D]
     lib.mrtlb_get_rates.argtypes = [P, D]
     lib.mrtlb_adjoint_forward.argtypes = [P, ctypes.c_long]
+    lib.mrtlb_adjoint_set_interval.argtypes = [P, ctypes.c_long]
     lib.mrtlb_adjoint_backward.argtypes = [P, P, P, D, P]
     lib.mrtlb_adjoint_release.argtypes = [P]
     lib.mrtlb_equilibrium_adjoint.argtypes = [P] + [P] * 9
@@ -324,6 +325,10 @@ def mrtlb_get_rates(ctx):
 
 def mrtlb_adjoint_forward(ctx, K):
     _check(load().mrtlb_adjoint_forward(ctx, int(K)), ctx)
+
+
+def mrtlb_adjoint_set_interval(ctx, S):
+    _check(load().mrtlb_adjoint_set_interval(ctx, int(S)), ctx)
 
 
 def mrtlb_adjoint_backward(ctx, dL_dmacros=None, dL_dfK=None, dL_df0=None):

@@ -96,8 +96,12 @@ class Simulation:
     def rates(self):
         return M.mrtlb_get_rates(self.ctx)
 
-    def adjoint_forward(self, K):
-        """Advance K steps storing sqrt(K) checkpoints for adjoint_backward."""
+    def adjoint_forward(self, K, interval=None):
+        """Advance K steps keeping what adjoint_backward needs: every state if
+        they fit in half the free device memory, else checkpoints every
+        ceil(sqrt(K)) steps; `interval` forces the segment length."""
+        if interval is not None:
+            M.mrtlb_adjoint_set_interval(self.ctx, interval)
         M.mrtlb_adjoint_forward(self.ctx, K)
 
     def adjoint_backward(self, dL_dmacros=None, dL_dfK=None, want_df0=True):

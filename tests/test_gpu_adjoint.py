@@ -52,11 +52,11 @@ def _state(cfg, seed):
     return fdlb.prepare(f0, _oracle_params(cfg))
 
 
-def _adjoint(cuda, cfg, f0, K, w=None, seed_macros=None):
+def _adjoint(cuda, cfg, f0, K, w=None, seed_macros=None, interval=None):
     import torch
     with Simulation(cfg) as sim:
         sim.set_f(f0)
-        sim.adjoint_forward(K)
+        sim.adjoint_forward(K, interval)
         dm = None if seed_macros is None else torch.from_numpy(seed_macros).to(cuda)
         dw = None if w is None else torch.from_numpy(w).to(cuda)
         ds, df0 = sim.adjoint_backward(dL_dmacros=dm, dL_dfK=dw)
@@ -86,14 +86,16 @@ def test_one_step_adjoint_dot_product(cuda, bc, version):
     assert np.all(ds[:4] == 0)
 
 
-def test_multi_step_adjoint_through_checkpoints(cuda):
-    """K = 7: checkpoints every 3 steps, segments 3 + 3 + 1 recomputed."""
+@pytest.mark.parametrize("interval", [3, 0])
+def test_multi_step_adjoint_through_checkpoints(cuda, interval):
+    """K = 7: segments 3 + 3 + 1 (the first two recomputed from checkpoints),
+    or all 7 states kept (automatic choice on a small grid)."""
     cfg = _cfg(70, 13, BCS["walls_y"])
     f0 = _state(cfg, 110)
     rng = np.random.default_rng(111)
     v = rng.standard_normal(f0.shape)
     w = rng.standard_normal(f0.shape)
-    ds, lam0 = _adjoint(cuda, cfg, f0, 7, w=w)
+    ds, lam0 = _adjoint(cuda, cfg, f0, 7, w=w, interval=interval)
     p = _oracle_params(cfg)
     Jv = fdlb.run(f0 + 1j * H * v, p, 7).imag / H
     lhs, rhs = float((w * Jv).sum()), float((lam0 * v).sum())
@@ -152,3 +154,31 @@ def test_adjoint_rejects_version_3(cuda):
         with pytest.raises(M.MrtlbError) as ei:
             sim.adjoint_forward(2)
         assert ei.value.code == M.MRTLB_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("interval", [2, 0])
+def test_backward_twice_after_one_forward(cuda, interval):
+    """A second backward pass with another seed after the same forward pass
+    must see the same states (the slots are refilled from checkpoints), on
+    the tiled step kernel (grid wide enough for it)."""
+    import torch
+    cfg = _cfg(300, 40, BCS["outflow_x"])
+    f0 = _state(cfg, 150)
+    rng = np.random.default_rng(151)
+    w1, w2 = rng.standard_normal(f0.shape), rng.standard_normal(f0.shape)
+    with Simulation(cfg) as sim:
+        sim.set_kernel(M.MRTLB_KERNEL_TILED)
+        sim.set_f(f0)
+        sim.adjoint_forward(5, interval)
+        fK = sim.get_f()
+        res = [sim.adjoint_backward(dL_dfK=torch.from_numpy(w).to(cuda)) for w in (w1, w2, w1)]
+    assert np.allclose(fK, fdlb.run(f0, _oracle_params(cfg), 5), rtol=0, atol=1e-12)
+    l1, l2, l3 = (r[1].cpu().numpy() for r in res)
+    assert np.array_equal(l1, l3)
+    # (the rate gradients are sums of FP64 atomics: equal up to their order)
+    assert np.allclose(res[0][0], res[2][0], rtol=1e-12, atol=0)
+    v = rng.standard_normal(f0.shape)
+    Jv = fdlb.run(f0 + 1j * H * v, _oracle_params(cfg), 5).imag / H
+    for w, lam in ((w1, l1), (w2, l2)):
+        lhs, rhs = float((w * Jv).sum()), float((lam * v).sum())
+        assert abs(lhs - rhs) < 1e-10 * np.abs(w * Jv).sum()
