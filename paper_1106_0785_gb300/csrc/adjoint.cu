@@ -28,24 +28,11 @@
 #include <vector>
 
 #include "adjoint.cuh"
+#include "adjoint_march.cuh"
 #include "ctx.h"
 
 namespace mrtlb {
 namespace {
-
-template <typename R>
-struct AdjCoef {
-  Coef<R> c;
-  R dt;
-  // derivatives of the modification factors dt (s7/s5 - 1), ... :
-  // dt/s5, dt/s6, dt s7/s5^2, dt s7/s6^2, dt s8/s5^2, dt s8/s6^2
-  R g[6];
-};
-
-template <typename R>
-__device__ __forceinline__ bool advanced(const Layout& L, int i, int j) {
-  return i >= L.i0 && i < L.i1 && j >= L.j0 && j < L.j1;
-}
 
 template <typename R>
 __device__ __forceinline__ void load16(const R* f, long long plane, long long at, R g[16]) {
@@ -77,14 +64,12 @@ __global__ void adj_prep_kernel(const R* __restrict__ ft, const R* __restrict__ 
     gst[at] = R(0);
     return;
   }
-  R lb[16], cb[16];
+  R lb[16];
   load16(lam, L.plane, at, lb);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) lb[q] = -lb[q];  // dL/dC = -lambda
-  inverse_T(a.c, lb, cb, false);
-  const R P = e - R(0.5) * (jx * ux + jy * uy);  // rho T
-  gsh[at] = cb[6] * a.c.mod[0] * P * ux + cb[7] * a.c.mod[3] * P * uy;
-  gst[at] = cb[6] * a.c.mod[1] * P * uy + cb[7] * a.c.mod[2] * P * ux;
+  R sh, sn;
+  gbar_node(a.c, lb, e - R(0.5) * (jx * ux + jy * uy), ux, uy, sh, sn);
+  gsh[at] = sh;
+  gst[at] = sn;
 }
 
 template <typename R>
@@ -101,115 +86,51 @@ __device__ __forceinline__ void adj_core_node(const R* __restrict__ ft, const R*
                                               const R* __restrict__ gsh, const R* __restrict__ gst,
                                               R* __restrict__ out, const Layout& L, const AdjCoef<R>& a, int i,
                                               int j, R G[16]) {
-  {
-    const Coef<R>& c = a.c;
-    const long long P = L.plane;
-    const long long at = L.node(i, j);
-    R g[16], lt[16];
-    load16(ft, P, at, g);
-    R rho, jx, jy, e;
-    conserved(g, rho, jx, jy, e);
-    // (ghost rows behind walls are never read by an advanced node and may be empty)
-    const R ir = (rho > R(0)) ? R(1) / rho : R(0);
-    const R ux = Ux[at], uy = Uy[at];
-    const R T = (e - R(0.5) * (jx * ux + jy * uy)) * ir;  // the linearisation point
+  const Coef<R>& c = a.c;
+  const long long P = L.plane;
+  const long long at = L.node(i, j);
+  const R ux = Ux[at], uy = Uy[at];
+  R g[16], lt[16];
+  load16(ft, P, at, g);
+  R rho = R(0);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) lt[q] = R(0);
-    if (advanced<R>(L, i, j)) {
-      R lp[16];
-      load16(lam, P, at, lp);
-      // (a) the node's own Lax-Wendroff weight
+  for (int q = 0; q < 16; ++q) rho += g[q];
+  // (ghost rows behind walls are never read by an advanced node and may be empty)
+  const R ir = (rho > R(0)) ? R(1) / rho : R(0);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        R w = R(1);
-        if (vx_of(q) != 0) w -= c.lw[q][0] + c.lw[q][1];
-        if (vy_of(q) != 0) w -= c.lw[q][2] + c.lw[q][3];
-        lt[q] = w * lp[q];
-      }
-      // forward quantities of the collision at p
-      const long long aE = at + 1, aW = at - 1, aN = at + L.pitch, aS = at - L.pitch;
-      const R shear = (Ux[aE] - Ux[aW]) * c.inv2dx - (Uy[aN] - Uy[aS]) * c.inv2dy;
-      const R strain = (Uy[aE] - Uy[aW]) * c.inv2dx + (Ux[aN] - Ux[aS]) * c.inv2dy;
-      Harm<R> h;
-      harmonics(g, h);
-      R m[16], eq[16];
-      moments(h, m);
-      equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eq);
-      const R Pp = rho * T;
-      // (b) collision transpose
-      R Cb[16], cb[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) Cb[q] = -lp[q];
-      inverse_T(c, Cb, cb, false);
-      R mb[16], eqb[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        mb[k] = (k >= 4) ? c.rate[k] * cb[k] : R(0);
-        eqb[k] = (k >= 4) ? -c.rate[k] * cb[k] : R(0);
-      }
-      EqIn<R> x{rho, ir, jx, jy, e, ux, uy, T};
-      EqIn<R> gi{R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-      if (c.modified) {
-        const R Pb = cb[6] * (c.mod[0] * ux * shear + c.mod[1] * uy * strain) +
-                     cb[7] * (c.mod[2] * ux * strain + c.mod[3] * uy * shear);
-        gi.ux += cb[6] * c.mod[0] * Pp * shear + cb[7] * c.mod[2] * Pp * strain;
-        gi.uy += cb[6] * c.mod[1] * Pp * strain + cb[7] * c.mod[3] * Pp * shear;
-        gi.rho += Pb * T;
-        gi.T += Pb * rho;
-      }
-      equilibrium_T(c, x, eqb, gi);
-      R rb, jxb, jyb, eb;
-      chain_primitive(x, gi, rb, jxb, jyb, eb);
-      mb[0] += rb;
-      mb[1] += jxb;
-      mb[2] += jyb;
-      mb[3] += eb;
-      Harm<R> hb;
-      moments_T(mb, hb);
-      R fb[16];
-      harmonics_T(hb, fb);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) lt[q] += fb[q];
-      // rate gradients: d f1 / d s_k through dt s_k (m_k - eq_k) and the
-      // modification factors dt (s7/s5 - 1), ... (dL/dC = -lambda)
-      const R dt = a.dt;
-#pragma unroll
-      for (int k = 4; k < 16; ++k) G[k] += dt * cb[k] * (m[k] - eq[k]);
-      if (c.modified) {
-        const R A0 = Pp * ux * shear, A1 = Pp * uy * strain;
-        const R A2 = Pp * ux * strain, A3 = Pp * uy * shear;
-        G[6] += cb[6] * (A0 * a.g[0] + A1 * a.g[1]);   // dt/s5, dt/s6
-        G[7] += cb[7] * (A2 * a.g[1] + A3 * a.g[0]);
-        G[4] -= cb[6] * A0 * a.g[2] + cb[7] * A3 * a.g[4];  // dt s7/s5^2, dt s8/s5^2
-        G[5] -= cb[6] * A1 * a.g[3] + cb[7] * A2 * a.g[5];  // dt s7/s6^2, dt s8/s6^2
-      }
-    }
-    // (a) neighbours' Lax-Wendroff weights on p
-    const int nbi[4] = {i - 1, i + 1, i, i};  // r = p - e_x (uses kE), p + e_x (kW), p - e_y (kN), p + e_y (kS)
-    const int nbj[4] = {j, j, j - 1, j + 1};
-#pragma unroll
-    for (int n = 0; n < 4; ++n) {
-      if (!advanced<R>(L, nbi[n], nbj[n])) continue;
-      const long long ar = L.node(nbi[n], nbj[n]);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        if (n < 2 && vx_of(q) == 0) continue;
-        if (n >= 2 && vy_of(q) == 0) continue;
-        lt[q] += c.lw[q][n] * lam[q * P + ar];
-      }
-    }
-    // (c) the modification at the neighbours, through u(p)
-    if (c.modified) {
-      const R uxb = c.inv2dx * (gbar_at(gsh, L, i - 1, j) - gbar_at(gsh, L, i + 1, j)) +
-                    c.inv2dy * (gbar_at(gst, L, i, j - 1) - gbar_at(gst, L, i, j + 1));
-      const R uyb = c.inv2dx * (gbar_at(gst, L, i - 1, j) - gbar_at(gst, L, i + 1, j)) -
-                    c.inv2dy * (gbar_at(gsh, L, i, j - 1) - gbar_at(gsh, L, i, j + 1));
-#pragma unroll
-      for (int q = 0; q < 16; ++q) lt[q] += (uxb * (R(vx_of(q)) - ux) + uyb * (R(vy_of(q)) - uy)) * ir;
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) out[q * P + at] = lt[q];
+  for (int q = 0; q < 16; ++q) lt[q] = R(0);
+  if (advanced<R>(L, i, j)) {
+    R lp[16];
+    load16(lam, P, at, lp);
+    const long long aE = at + 1, aW = at - 1, aN = at + L.pitch, aS = at - L.pitch;
+    const R shear = (Ux[aE] - Ux[aW]) * c.inv2dx - (Uy[aN] - Uy[aS]) * c.inv2dy;
+    const R strain = (Uy[aE] - Uy[aW]) * c.inv2dx + (Ux[aN] - Ux[aS]) * c.inv2dy;
+    collision_T_node(a, g, lp, ux, uy, shear, strain, lt, G);
   }
+  // (a) neighbours' Lax-Wendroff weights on p
+  const int nbi[4] = {i - 1, i + 1, i, i};  // r = p - e_x (uses kE), p + e_x (kW), p - e_y (kN), p + e_y (kS)
+  const int nbj[4] = {j, j, j - 1, j + 1};
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    if (!advanced<R>(L, nbi[n], nbj[n])) continue;
+    const long long ar = L.node(nbi[n], nbj[n]);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      if (n < 2 && vx_of(q) == 0) continue;
+      if (n >= 2 && vy_of(q) == 0) continue;
+      lt[q] += c.lw[q][n] * lam[q * P + ar];
+    }
+  }
+  // (c) the modification at the neighbours, through u(p)
+  if (c.modified) {
+    const R uxb = c.inv2dx * (gbar_at(gsh, L, i - 1, j) - gbar_at(gsh, L, i + 1, j)) +
+                  c.inv2dy * (gbar_at(gst, L, i, j - 1) - gbar_at(gst, L, i, j + 1));
+    const R uyb = c.inv2dx * (gbar_at(gst, L, i - 1, j) - gbar_at(gst, L, i + 1, j)) -
+                  c.inv2dy * (gbar_at(gsh, L, i, j - 1) - gbar_at(gsh, L, i, j + 1));
+    velocity_T(uxb, uyb, ux, uy, ir, lt);
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) out[q * P + at] = lt[q];
 }
 
 #ifndef MRTLB_ADJ_MINB
@@ -233,15 +154,23 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MRTLB_ADJ_MINB : 2)
     if (i <= L.nx && !((i < 0 || i >= L.nx) && (j < 0 || j >= L.ny)))
       adj_core_node(ft, lam, Ux, Uy, gsh, gst, out, L, a, i, j, G);
   }
-  // warp sums of the rate gradients, one FP64 atomic per warp and rate
-#pragma unroll
-  for (int k = 4; k < 16; ++k) {
-    R v = G[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v != R(0)) atomicAdd(gacc + k, (double)v);
-  }
+  flush_rate_gradients(G, gacc);
 }
+
+// Adjoint march shapes: 128-column strips (FP32; 64 for FP64, same box
+// bytes), 4 B(f) slots and 6 lambda slots, about 95 KB of shared memory.
+#ifndef MRTLB_ADJ_BX
+#define MRTLB_ADJ_BX 128
+#endif
+#ifndef MRTLB_ADJ_NF
+#define MRTLB_ADJ_NF 4
+#endif
+#ifndef MRTLB_ADJ_NL
+#define MRTLB_ADJ_NL 6
+#endif
+template <typename R> struct AdjTile;
+template <> struct AdjTile<float> { static constexpr int BX = MRTLB_ADJ_BX, NF = MRTLB_ADJ_NF, NL = MRTLB_ADJ_NL; };
+template <> struct AdjTile<double> { static constexpr int BX = 64, NF = 4, NL = 6; };
 
 // B^T, ghosts: every edge node collects the adjoints of the ghost cells that
 // mirror it; the ghost cells are cleared.
@@ -415,6 +344,11 @@ struct mrtlb_adjoint_state {
   void* uy = nullptr;
   double* gacc = nullptr;
   int core_blocks = 1;       // resident blocks of the core kernel on the device
+  // the fused adjoint march: read maps of every slot and of both lambdas
+  bool march = false;
+  std::vector<CUtensorMap> fmap;
+  CUtensorMap lmap[2];
+  int m_nstrips = 0, m_nseg = 0, m_seglen = 0;
 };
 
 namespace {
@@ -471,27 +405,79 @@ AdjCoef<R> adj_coef(const mrtlb_ctx* c, const Coef<R>& k) {
   return a;
 }
 
-// one adjoint step: lam_in (dL/df^{n+1}) -> lam_out (dL/df^n), ft = B(f^n)
 template <typename R>
-void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, const R* ft, const R* lam_in, R* lam_out,
-                  const Coef<R>& k, cudaStream_t st) {
+void launch_adj_march(const mrtlb_adjoint_state* a, const Layout& L, const CUtensorMap& fm, const CUtensorMap& lm,
+                      R* out, const AdjCoef<R>& ac, int* err, cudaStream_t st) {
+  constexpr int BX = AdjTile<R>::BX, NF = AdjTile<R>::NF, NL = AdjTile<R>::NL;
+  using SM = AdjSmem<R, BX, NF, NL>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SM::bytes);
+    attr = true;
+  }
+  dim3 grid(a->m_nstrips, a->m_nseg);
+  adj_march_kernel<R, BX, NF, NL><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
+}
+
+// one adjoint step: lambda[li] (dL/df^{n+1}) -> lambda[li ^ 1] (dL/df^n),
+// ft = B(f^n) in slot n
+template <typename R>
+void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, long n, int li, const Coef<R>& k, cudaStream_t st) {
   const Layout& L = c->L;
   const AdjCoef<R> ac = adj_coef<R>(c, k);
-  dim3 g2((L.nx + 2 + 127) / 128, L.ny + 2);
-  adj_prep_kernel<R><<<g2, 128, 0, st>>>(ft, lam_in, (R*)a->ux, (R*)a->uy, (R*)a->gsh, (R*)a->gst, L, ac);
-  const int ntiles = (int)(g2.x * g2.y);
-  const int grid = std::min(ntiles, a->core_blocks);
-  adj_core_kernel<R><<<grid, 128, 0, st>>>(ft, lam_in, (const R*)a->ux, (const R*)a->uy, (const R*)a->gsh,
-                                           (const R*)a->gst, lam_out, L, ac, a->gacc, (int)g2.x, ntiles);
+  const R* ft = (const R*)((char*)a->seg + (size_t)n * c->state_bytes);
+  const R* lam_in = (const R*)a->lam[li];
+  R* lam_out = (R*)a->lam[li ^ 1];
+  if (a->march) {
+    launch_adj_march<R>(a, L, a->fmap[n], a->lmap[li], lam_out, ac, c->err, st);
+  } else {
+    dim3 g2((L.nx + 2 + 127) / 128, L.ny + 2);
+    adj_prep_kernel<R><<<g2, 128, 0, st>>>(ft, lam_in, (R*)a->ux, (R*)a->uy, (R*)a->gsh, (R*)a->gst, L, ac);
+    const int ntiles = (int)(g2.x * g2.y);
+    const int grid = std::min(ntiles, a->core_blocks);
+    adj_core_kernel<R><<<grid, 128, 0, st>>>(ft, lam_in, (const R*)a->ux, (const R*)a->uy, (const R*)a->gsh,
+                                             (const R*)a->gst, lam_out, L, ac, a->gacc, (int)g2.x, ntiles);
+  }
   const int perim = 2 * L.nx + 2 * L.ny;
   adj_ghosts_kernel<R><<<(perim + 127) / 128, 128, 0, st>>>(lam_out, L);
   dim3 g3((std::max(L.nx, L.ny + 2) + 255) / 256, 16);
   adj_clear_ghosts_kernel<R><<<g3, 256, 0, st>>>(lam_out, L);
   for (int s = 0; s < 4; ++s)
     if (L.bc[s] == BC_WALL) {
-      const int n = (s < 2) ? L.ny : L.nx;
-      adj_walls_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(lam_out, ft, L, c->c64, c->walls, s);
+      const int nn = (s < 2) ? L.ny : L.nx;
+      adj_walls_kernel<R><<<(nn + 127) / 128, 128, 0, st>>>(lam_out, ft, L, c->c64, c->walls, s);
     }
+}
+
+// Maps and row segments of the adjoint march; false if it cannot run.
+template <typename R>
+bool plan_adj_march(mrtlb_ctx* c, mrtlb_adjoint_state* a) {
+  constexpr int BX = AdjTile<R>::BX, NF = AdjTile<R>::NF, NL = AdjTile<R>::NL;
+  using SM = AdjSmem<R, BX, NF, NL>;
+  const Layout& L = c->L;
+  const int es = (int)sizeof(R);
+  a->fmap.resize((size_t)(a->S + 1) & ~(size_t)1);
+  for (long n = 0; n < a->S; n += 2) {
+    void* s0 = (char*)a->seg + (size_t)n * c->state_bytes;
+    void* s1 = (char*)a->seg + (size_t)std::min(n + 1, a->S - 1) * c->state_bytes;
+    if (encode_row_maps(L, es, s0, s1, BX, &a->fmap[n]) != 0) return false;
+  }
+  if (encode_row_maps(L, es, a->lam[0], a->lam[1], BX, a->lmap) != 0) return false;
+  if (cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SM::bytes) != cudaSuccess)
+    return false;
+  int dev = 0, nsm = 1, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj_march_kernel<R, BX, NF, NL>, BX, SM::bytes);
+  if (per < 1) return false;
+  const int rows = L.ny + 2;  // output rows -1 .. ny
+  a->m_nstrips = (L.nx + 2 + BX - 1) / BX;
+  int nseg = std::max(1, nsm * per / a->m_nstrips);
+  a->m_seglen = std::max(8, (rows + nseg - 1) / nseg);
+  a->m_nseg = (rows + a->m_seglen - 1) / a->m_seglen;
+  return true;
 }
 
 template <typename R>
@@ -549,8 +535,7 @@ int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, 
       adj_walls_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(lam0, fK, L, c->c64, c->walls, s);
     }
   ACK(cudaGetLastError(), "adjoint seed");
-  R* lin = lam0;
-  R* lout = lam1;
+  int li = 0;  // lambda[li] holds dL/df of the latest state reached
   const long K = a->K, S = a->S;
   for (long sgi = a->nseg - 1; sgi >= 0; --sgi) {
     const long t0 = sgi * S;
@@ -561,17 +546,20 @@ int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, 
       a->held = sgi;
     }
     for (long n = len - 1; n >= 0; --n) {
-      adjoint_step<R>(c, a, slot<R>(c, a, n), lin, lout, k, st);
-      std::swap(lin, lout);
+      adjoint_step<R>(c, a, n, li, k, st);
+      li ^= 1;
     }
   }
   ACK(cudaGetLastError(), "adjoint steps");
   if (dL_df0) {
     dim3 gd((L.nx + 127) / 128, L.ny, 16);
-    adj_dense_kernel<R><<<gd, 128, 0, st>>>(lin, dL_df0, L, 1);
+    adj_dense_kernel<R><<<gd, 128, 0, st>>>((R*)a->lam[li], dL_df0, L, 1);
   }
   if (dL_ds) ACK(cudaMemcpyAsync(dL_ds, a->gacc, 16 * sizeof(double), cudaMemcpyDeviceToHost, st), "copy grads");
+  int h = 0;
+  ACK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, st), "read error word");
   ACK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (h & ERRBIT_TIMEOUT) return afail(c, MRTLB_ERR_TIMEOUT, "a bounded device-side wait gave up");
   return MRTLB_OK;
 }
 
@@ -621,6 +609,7 @@ int forward_impl(mrtlb_ctx* c, long K) {
       }
     }
   }
+  a->march = a->tiled && plan_adj_march<R>(c, a);
   // all segments but the last: checkpoint, then the context's own time loop
   for (long sg = 0; sg + 1 < a->nseg; ++sg) {
     ACK(cudaMemcpyAsync(a->ckpt[sg], c->f[c->cur], sb, cudaMemcpyDeviceToDevice, st), "store checkpoint");

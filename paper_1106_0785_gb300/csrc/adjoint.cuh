@@ -7,6 +7,7 @@
 // and the transpose of the moment rows is a radial combination per family.
 #pragma once
 
+#include "kernels.cuh"
 #include "physics.cuh"
 
 namespace mrtlb {
@@ -162,6 +163,149 @@ __device__ __forceinline__ void chain_primitive(const EqIn<R>& x, const EqIn<R>&
   rb = g.rho + Nb * x.e - irb * x.ir * x.ir;
   jxb -= Nb * x.jx;
   jyb -= Nb * x.jy;
+}
+
+// Coefficients of one adjoint step.
+template <typename R>
+struct AdjCoef {
+  Coef<R> c;
+  R dt;
+  // derivatives of the modification factors dt (s7/s5 - 1), ... :
+  // dt/s5, dt/s6, dt s7/s5^2, dt s7/s6^2, dt s8/s5^2, dt s8/s6^2
+  R g[6];
+};
+
+template <typename R>
+__device__ __forceinline__ bool advanced(const Layout& L, int i, int j) {
+  return i >= L.i0 && i < L.i1 && j >= L.j0 && j < L.j1;
+}
+
+// Rows 6 and 7 of inverse_T (all the modification needs): only the X and
+// Y harmonics of fb enter them.
+template <typename R>
+__device__ __forceinline__ void inverse_T_67(const Coef<R>& c, const R fb[16], R& m6, R& m7) {
+  m6 = R(0);
+  m7 = R(0);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const R a0 = fb[4 * s + 0], a1 = fb[4 * s + 1], a2 = fb[4 * s + 2], a3 = fb[4 * s + 3];
+    R X, Y;
+    if (s == 0 || s == 2) {
+      X = a0 - a2;
+      Y = a1 - a3;
+    } else {
+      X = (a0 + a3) - (a1 + a2);
+      Y = (a0 + a1) - (a2 + a3);
+    }
+    m6 += c.invX[s][1] * X;
+    m7 += c.invY[s][1] * Y;
+  }
+}
+
+// Adjoints of the two strain combinations of the modification at an
+// advanced node r with adjoint lambda (dL/dC = -lambda), rho T = P:
+//   gsh = dL/d(du_x/dx - du_y/dy),  gst = dL/d(du_y/dx + du_x/dy).
+template <typename R>
+__device__ __forceinline__ void gbar_node(const Coef<R>& c, const R lam[16], R P, R ux, R uy, R& gsh, R& gst) {
+  R c6, c7;
+  inverse_T_67(c, lam, c6, c7);
+  c6 = -c6;
+  c7 = -c7;
+  gsh = c6 * c.mod[0] * P * ux + c7 * c.mod[3] * P * uy;
+  gst = c6 * c.mod[1] * P * uy + c7 * c.mod[2] * P * ux;
+}
+
+// At an advanced node p with state g = B(f)(p), adjoint lp = lambda(p),
+// velocity u(p) and the two strain combinations of the forward step:
+// lt = (1 - sum_n k_qn) lp_q - (dC/dg)^T lp  (Lax-Wendroff self weight and
+// collision transpose, the temperature linearised at T = (e - j.u/2)/rho),
+// and the rate gradients of the node added to G[4..15].
+template <typename R>
+__device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[16], const R lp[16], R ux, R uy,
+                                                 R shear, R strain, R lt[16], R G[16]) {
+  const Coef<R>& c = a.c;
+  R rho, jx, jy, e;
+  conserved(g, rho, jx, jy, e);
+  const R ir = R(1) / rho;
+  const R T = (e - R(0.5) * (jx * ux + jy * uy)) * ir;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    R w = R(1);
+    if (vx_of(q) != 0) w -= c.lw[q][0] + c.lw[q][1];
+    if (vy_of(q) != 0) w -= c.lw[q][2] + c.lw[q][3];
+    lt[q] = w * lp[q];
+  }
+  Harm<R> h;
+  harmonics(g, h);
+  R m[16], eq[16];
+  moments(h, m);
+  equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eq);
+  const R Pp = rho * T;
+  R Cb[16], cb[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) Cb[q] = -lp[q];
+  inverse_T(c, Cb, cb, false);
+  R mb[16], eqb[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    mb[k] = (k >= 4) ? c.rate[k] * cb[k] : R(0);
+    eqb[k] = (k >= 4) ? -c.rate[k] * cb[k] : R(0);
+  }
+  EqIn<R> x{rho, ir, jx, jy, e, ux, uy, T};
+  EqIn<R> gi{R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+  if (c.modified) {
+    const R Pb = cb[6] * (c.mod[0] * ux * shear + c.mod[1] * uy * strain) +
+                 cb[7] * (c.mod[2] * ux * strain + c.mod[3] * uy * shear);
+    gi.ux += cb[6] * c.mod[0] * Pp * shear + cb[7] * c.mod[2] * Pp * strain;
+    gi.uy += cb[6] * c.mod[1] * Pp * strain + cb[7] * c.mod[3] * Pp * shear;
+    gi.rho += Pb * T;
+    gi.T += Pb * rho;
+  }
+  equilibrium_T(c, x, eqb, gi);
+  R rb, jxb, jyb, eb;
+  chain_primitive(x, gi, rb, jxb, jyb, eb);
+  mb[0] += rb;
+  mb[1] += jxb;
+  mb[2] += jyb;
+  mb[3] += eb;
+  Harm<R> hb;
+  moments_T(mb, hb);
+  R fb[16];
+  harmonics_T(hb, fb);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) lt[q] += fb[q];
+  // rate gradients: d f1 / d s_k through dt s_k (m_k - eq_k) and the
+  // modification factors dt (s7/s5 - 1), ... (dL/dC = -lambda)
+  const R dt = a.dt;
+#pragma unroll
+  for (int k = 4; k < 16; ++k) G[k] += dt * cb[k] * (m[k] - eq[k]);
+  if (c.modified) {
+    const R A0 = Pp * ux * shear, A1 = Pp * uy * strain;
+    const R A2 = Pp * ux * strain, A3 = Pp * uy * shear;
+    G[6] += cb[6] * (A0 * a.g[0] + A1 * a.g[1]);        // dt/s5, dt/s6
+    G[7] += cb[7] * (A2 * a.g[1] + A3 * a.g[0]);
+    G[4] -= cb[6] * A0 * a.g[2] + cb[7] * A3 * a.g[4];  // dt s7/s5^2, dt s8/s5^2
+    G[5] -= cb[6] * A1 * a.g[3] + cb[7] * A2 * a.g[5];  // dt s7/s6^2, dt s8/s6^2
+  }
+}
+
+// Adjoint of u = j / rho at p carried to f(p): lt_q += (ub . (v_q - u)) / rho.
+template <typename R>
+__device__ __forceinline__ void velocity_T(R uxb, R uyb, R ux, R uy, R ir, R lt[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) lt[q] += (uxb * (R(vx_of(q)) - ux) + uyb * (R(vy_of(q)) - uy)) * ir;
+}
+
+// Sum the rate gradients over the warp; one FP64 atomic per warp and rate.
+template <typename R>
+__device__ __forceinline__ void flush_rate_gradients(const R G[16], double* gacc) {
+#pragma unroll
+  for (int k = 4; k < 16; ++k) {
+    R v = G[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != R(0)) atomicAdd(gacc + k, (double)v);
+  }
 }
 
 }  // namespace mrtlb

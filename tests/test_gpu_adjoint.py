@@ -52,9 +52,16 @@ def _state(cfg, seed):
     return fdlb.prepare(f0, _oracle_params(cfg))
 
 
-def _adjoint(cuda, cfg, f0, K, w=None, seed_macros=None, interval=None):
+KERNELS = {"plain": M.MRTLB_KERNEL_PLAIN, "tiled": M.MRTLB_KERNEL_TILED}
+
+
+def _adjoint(cuda, cfg, f0, K, w=None, seed_macros=None, interval=None, kernel="auto"):
+    """The tiled kernel choice runs the adjoint as the fused row march, the
+    plain one as the two-pass gather."""
     import torch
     with Simulation(cfg) as sim:
+        if kernel != "auto":
+            sim.set_kernel(KERNELS[kernel])
         sim.set_f(f0)
         sim.adjoint_forward(K, interval)
         dm = None if seed_macros is None else torch.from_numpy(seed_macros).to(cuda)
@@ -63,15 +70,16 @@ def _adjoint(cuda, cfg, f0, K, w=None, seed_macros=None, interval=None):
         return ds, df0.cpu().numpy()
 
 
+@pytest.mark.parametrize("kernel", list(KERNELS))
 @pytest.mark.parametrize("bc", list(BCS))
 @pytest.mark.parametrize("version", [1, 2])
-def test_one_step_adjoint_dot_product(cuda, bc, version):
+def test_one_step_adjoint_dot_product(cuda, bc, version, kernel):
     cfg = _cfg(140, 21, BCS[bc], version)
     f0 = _state(cfg, 100)
     rng = np.random.default_rng(101)
     v = rng.standard_normal(f0.shape)
     w = rng.standard_normal(f0.shape)
-    ds, lam0 = _adjoint(cuda, cfg, f0, 1, w=w)
+    ds, lam0 = _adjoint(cuda, cfg, f0, 1, w=w, kernel=kernel)
     p = _oracle_params(cfg)
     Jv = fdlb.step(f0 + 1j * H * v, p).imag / H
     lhs, rhs = float((w * Jv).sum()), float((lam0 * v).sum())
@@ -86,8 +94,9 @@ def test_one_step_adjoint_dot_product(cuda, bc, version):
     assert np.all(ds[:4] == 0)
 
 
+@pytest.mark.parametrize("kernel", list(KERNELS))
 @pytest.mark.parametrize("interval", [3, 0])
-def test_multi_step_adjoint_through_checkpoints(cuda, interval):
+def test_multi_step_adjoint_through_checkpoints(cuda, interval, kernel):
     """K = 7: segments 3 + 3 + 1 (the first two recomputed from checkpoints),
     or all 7 states kept (automatic choice on a small grid)."""
     cfg = _cfg(70, 13, BCS["walls_y"])
@@ -95,7 +104,7 @@ def test_multi_step_adjoint_through_checkpoints(cuda, interval):
     rng = np.random.default_rng(111)
     v = rng.standard_normal(f0.shape)
     w = rng.standard_normal(f0.shape)
-    ds, lam0 = _adjoint(cuda, cfg, f0, 7, w=w, interval=interval)
+    ds, lam0 = _adjoint(cuda, cfg, f0, 7, w=w, interval=interval, kernel=kernel)
     p = _oracle_params(cfg)
     Jv = fdlb.run(f0 + 1j * H * v, p, 7).imag / H
     lhs, rhs = float((w * Jv).sum()), float((lam0 * v).sum())
@@ -107,14 +116,15 @@ def test_multi_step_adjoint_through_checkpoints(cuda, interval):
     assert abs(ds[k] - float((w * dF).sum())) < 1e-9 * np.abs(w * dF).sum()
 
 
-def test_macro_seed(cuda):
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_macro_seed(cuda, kernel):
     """L = sum(a rho + b ux + c uy + d T) of the final macroscopic fields."""
     cfg = _cfg(66, 17, BCS["outflow_x"])
     f0 = _state(cfg, 120)
     rng = np.random.default_rng(121)
     weights = rng.standard_normal((4, cfg.ny, cfg.nx))
     v = rng.standard_normal(f0.shape)
-    ds, lam0 = _adjoint(cuda, cfg, f0, 4, seed_macros=weights)
+    ds, lam0 = _adjoint(cuda, cfg, f0, 4, seed_macros=weights, kernel=kernel)
     p = _oracle_params(cfg)
     fK = fdlb.run(f0 + 1j * H * v, p, 4)
     dL = float(sum((weights[k] * m).sum() for k, m in enumerate(fdlb.macros(fK))).imag / H)
@@ -137,13 +147,14 @@ def test_equilibrium_adjoint(cuda):
     assert abs(lhs - rhs) < 1e-11 * np.abs(lam * jf).sum()
 
 
-def test_fp32_adjoint_close_to_fp64(cuda):
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_fp32_adjoint_close_to_fp64(cuda, kernel):
     cfg64 = _cfg(140, 21, BCS["walls_y"])
     f0 = _state(cfg64, 140)
     w = np.random.default_rng(141).standard_normal(f0.shape)
     ds64, l64 = _adjoint(cuda, cfg64, f0, 5, w=w)
     cfg32 = _cfg(140, 21, BCS["walls_y"], precision="fp32")
-    ds32, l32 = _adjoint(cuda, cfg32, f0.astype(np.float32), 5, w=w)
+    ds32, l32 = _adjoint(cuda, cfg32, f0.astype(np.float32), 5, w=w, kernel=kernel)
     assert np.abs(l32 - l64).max() < 1e-4 * np.abs(l64).max()
     assert np.allclose(ds32[4:], ds64[4:], rtol=1e-3, atol=1e-4 * np.abs(ds64).max())
 
@@ -182,3 +193,23 @@ def test_backward_twice_after_one_forward(cuda, interval):
     for w, lam in ((w1, l1), (w2, l2)):
         lhs, rhs = float((w * Jv).sum()), float((lam * v).sum())
         assert abs(lhs - rhs) < 1e-10 * np.abs(w * Jv).sum()
+
+
+def test_march_matches_two_pass_on_a_ragged_grid(cuda):
+    """FP32, 1030 x 260 (ragged strips and row segments), 3 steps: the fused
+    row march and the two-pass gather give the same adjoint."""
+    import torch
+    cfg = _cfg(1030, 260, BCS["walls_x"], precision="fp32")
+    f0 = _state(_cfg(1030, 260, BCS["walls_x"]), 160).astype(np.float32)
+    w = np.random.default_rng(161).standard_normal(f0.shape)
+    res = {}
+    for kernel in KERNELS:
+        with Simulation(cfg) as sim:
+            sim.set_kernel(KERNELS[kernel])
+            sim.set_f(f0)
+            sim.adjoint_forward(3)
+            res[kernel] = sim.adjoint_backward(dL_dfK=torch.from_numpy(w).to(cuda))
+    (dp, lp), (dt, lt) = res["plain"], res["tiled"]
+    lp, lt = lp.cpu().numpy(), lt.cpu().numpy()
+    assert np.abs(lp - lt).max() < 1e-5 * np.abs(lp).max()
+    assert np.allclose(dp[4:], dt[4:], rtol=1e-4, atol=1e-6 * np.abs(dp).max())
