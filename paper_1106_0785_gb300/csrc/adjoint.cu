@@ -158,22 +158,26 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MRTLB_ADJ_MINB : 2)
 }
 
 // Adjoint march shapes: 128-column strips (FP32; 64 for FP64, same box
-// bytes), 4 B(f) slots and 6 lambda slots, about 95 KB of shared memory.
+// bytes), 3 B(f) slots and 4 lambda slots: about 71 KB of shared memory,
+// three CTAs per SM (measured on GB300 against 4+6, 4+4 slots and 64-,
+// 96-, 256-column strips).
 #ifndef MRTLB_ADJ_BX
 #define MRTLB_ADJ_BX 128
 #endif
 #ifndef MRTLB_ADJ_NF
-#define MRTLB_ADJ_NF 4
+#define MRTLB_ADJ_NF 3
 #endif
 #ifndef MRTLB_ADJ_NL
-#define MRTLB_ADJ_NL 6
+#define MRTLB_ADJ_NL 4
 #endif
 template <typename R> struct AdjTile;
 template <> struct AdjTile<float> { static constexpr int BX = MRTLB_ADJ_BX, NF = MRTLB_ADJ_NF, NL = MRTLB_ADJ_NL; };
-template <> struct AdjTile<double> { static constexpr int BX = 64, NF = 4, NL = 6; };
+template <> struct AdjTile<double> { static constexpr int BX = 64, NF = 3, NL = 4; };
 
 // B^T, ghosts: every edge node collects the adjoints of the ghost cells that
-// mirror it; the ghost cells are cleared.
+// mirror it (plane q = blockIdx.y).  The ghost cells keep their values:
+// lambda is only ever read at advanced nodes, and every step overwrites
+// the whole padded grid [-1, nx] x [-1, ny].
 template <typename R>
 __global__ void adj_ghosts_kernel(R* lam, Layout L) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -189,26 +193,12 @@ __global__ void adj_ghosts_kernel(R* lam, Layout L) {
   if (t >= L.nx && t < 2 * L.nx && L.ny == 1) return;
   if (t >= 2 * L.nx + L.ny && L.nx == 1) return;
   const GhostTargets g = ghost_targets(L, i, j);
-  R* p = lam + L.node(i, j);
-  for (int s = 0; s < 4; ++s) {
-    if (!g.w[s]) continue;
-    for (int q = 0; q < 16; ++q) p[q * L.plane] += p[q * L.plane + g.off[s]];
-  }
-}
-
-template <typename R>
-__global__ void adj_clear_ghosts_kernel(R* lam, Layout L) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int q = blockIdx.y;
-  R* lq = lam + q * L.plane;
-  if (t < L.ny + 2) {
-    lq[(long long)t * L.pitch + L.xoff - 1] = R(0);
-    lq[(long long)t * L.pitch + L.xoff + L.nx] = R(0);
-  }
-  if (t < L.nx) {
-    lq[L.xoff + t] = R(0);
-    lq[(long long)(L.ny + 1) * L.pitch + L.xoff + t] = R(0);
-  }
+  if (!g.any()) return;
+  R* p = lam + (long long)blockIdx.y * L.plane + L.node(i, j);
+  R v = *p;
+  for (int s = 0; s < 4; ++s)
+    if (g.w[s]) v += p[g.off[s]];
+  *p = v;
 }
 
 // B^T, walls on one side: the wall node w was NEE(f(a)) of its fluid
@@ -262,7 +252,8 @@ __global__ void adj_walls_kernel(R* lam, const R* __restrict__ ft, Layout L, Coe
   }
 }
 
-// Seed: lambda = (d(rho, u_x, u_y, T)/df)^T (dL/d macros) on every node.
+// Seed: lambda = (d(rho, u_x, u_y, T)/df)^T (dL/d macros) on every node,
+// in the precision of the state.
 template <typename R>
 __global__ void adj_seed_macros_kernel(const R* __restrict__ ft, const double* __restrict__ seed, R* lam,
                                        Layout L) {
@@ -270,20 +261,20 @@ __global__ void adj_seed_macros_kernel(const R* __restrict__ ft, const double* _
   const int j = blockIdx.y;
   if (i >= L.nx) return;
   const long long n = (long long)L.nx * L.ny, t = (long long)j * L.nx + i, at = L.node(i, j);
-  double g[16];
+  R g[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) g[q] = (double)ft[q * L.plane + at];
-  double rho, jx, jy, e;
+  for (int q = 0; q < 16; ++q) g[q] = ft[q * L.plane + at];
+  R rho, jx, jy, e;
   conserved(g, rho, jx, jy, e);
-  const double ir = 1.0 / rho;
-  EqIn<double> x{rho, ir, jx, jy, e, jx * ir, jy * ir, temperature(rho, jx, jy, e, ir)};
-  EqIn<double> gi{seed[t], 0, 0, 0, 0, seed[n + t], seed[2 * n + t], seed[3 * n + t]};
-  double rb, jxb, jyb, eb;
+  const R ir = R(1) / rho;
+  EqIn<R> x{rho, ir, jx, jy, e, jx * ir, jy * ir, temperature(rho, jx, jy, e, ir)};
+  EqIn<R> gi{(R)seed[t], R(0), R(0), R(0), R(0), (R)seed[n + t], (R)seed[2 * n + t], (R)seed[3 * n + t]};
+  R rb, jxb, jyb, eb;
   chain_primitive(x, gi, rb, jxb, jyb, eb);
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
-    const double vx = vx_of(q), vy = vy_of(q);
-    lam[q * L.plane + at] = (R)(rb + jxb * vx + jyb * vy + eb * 0.5 * (vx * vx + vy * vy));
+    const R vx = vx_of(q), vy = vy_of(q);
+    lam[q * L.plane + at] = rb + jxb * vx + jyb * vy + eb * R(0.5) * (vx * vx + vy * vy);
   }
 }
 
@@ -440,9 +431,7 @@ void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, long n, int li, const Co
                                              (const R*)a->gst, lam_out, L, ac, a->gacc, (int)g2.x, ntiles);
   }
   const int perim = 2 * L.nx + 2 * L.ny;
-  adj_ghosts_kernel<R><<<(perim + 127) / 128, 128, 0, st>>>(lam_out, L);
-  dim3 g3((std::max(L.nx, L.ny + 2) + 255) / 256, 16);
-  adj_clear_ghosts_kernel<R><<<g3, 256, 0, st>>>(lam_out, L);
+  adj_ghosts_kernel<R><<<dim3((perim + 127) / 128, 16), 128, 0, st>>>(lam_out, L);
   for (int s = 0; s < 4; ++s)
     if (L.bc[s] == BC_WALL) {
       const int nn = (s < 2) ? L.ny : L.nx;
@@ -473,7 +462,7 @@ bool plan_adj_march(mrtlb_ctx* c, mrtlb_adjoint_state* a) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj_march_kernel<R, BX, NF, NL>, BX, SM::bytes);
   if (per < 1) return false;
   const int rows = L.ny + 2;  // output rows -1 .. ny
-  a->m_nstrips = (L.nx + 2 + BX - 1) / BX;
+  a->m_nstrips = (L.nx + 2 + SM::SX - 1) / SM::SX;
   int nseg = std::max(1, nsm * per / a->m_nstrips);
   a->m_seglen = std::max(8, (rows + nseg - 1) / nseg);
   a->m_nseg = (rows + a->m_seglen - 1) / a->m_seglen;

@@ -9,9 +9,12 @@
 // computed per row as the row arrives and kept in a 4-row shared ring, so
 // that one kernel reads B(f) and lambda once and writes lambda~ once.
 //
-// A CTA owns output columns x0-1 .. x0+BX-2 (thread t: x = x0-1+t; the
-// strips of all CTAs tile the padded columns -1 .. nx) and a segment of
-// output rows [ja, jb) within -1 .. ny.  Rows ja-1 .. jb stream in through
+// Thread t of a CTA owns column x = x0-2+t: it computes u, 1/rho and gbar
+// of that column for every row, and lambda~ of its column if 1 <= t <= SX
+// (SX = BX-4 output columns x0-1 .. x0+SX-2; strips start at multiples of
+// SX, a multiple of 16 bytes, and overlap by 4 columns so that every
+// neighbour an output needs is prepared by a thread of the same CTA).  A CTA
+// also owns a segment of output rows [ja, jb) within -1 .. ny.  Rows ja-1 .. jb stream in through
 // cp.async.bulk.tensor, one 3D box per row and array (16 planes x BX + 2 HL
 // columns starting at x0 - HL, 16-byte aligned):
 //   * B(f) rows into an NF-slot ring: row r is read by the prep of r (own
@@ -20,8 +23,8 @@
 //     by the cores of rows r-1, r, r+1.
 // Rows outside the padded grid (-2 and ny+1) load as zeros (TMA fill) and
 // are never used by an advanced node.  Per output row j the CTA:
-//   1. waits for row j+1, computes u, 1/rho, gbar of row j+1 for columns
-//      x0-2 .. x0+BX-1 into the ring (lanes 0, 1 take the two halo columns);
+//   1. waits for row j+1, computes u, 1/rho, gbar of row j+1 for its BX
+//      columns into the ring;
 //   2. agrees at a barrier (barrier-or of expired waits), refills the slots
 //      freed by row j-1 (B(f)) and j-2 (lambda);
 //   3. computes lambda~(x, j) from the rings and writes its 16 planes.
@@ -42,7 +45,8 @@ struct AdjSmem {
   static constexpr int HL = 16 / (int)sizeof(R);  // halo columns either side of the box
   static constexpr int BW = BX + 2 * HL;          // box width (elements)
   static constexpr int ROW = 16 * BW;             // elements of one row (16 planes)
-  static constexpr int PW = BX + 2;               // prep columns x0-2 .. x0+BX-1
+  static constexpr int SX = BX - 4;               // output columns per strip (strip stride)
+  static constexpr int PW = BX;                   // prep columns x0-2 .. x0+BX-3
   static constexpr int NP = 5;                    // u_x, u_y, gbar_shear, gbar_strain, 1/rho
   static constexpr int PROW = NP * PW;
   static constexpr size_t row_bytes = (size_t)ROW * sizeof(R);
@@ -65,6 +69,7 @@ struct AdjMarch {
   R* out;
   Layout L;
   int t, x0, x, boxx, r_first, r_last, f_issued, l_issued;
+  bool out_col;  // the thread's column is an output of this strip
 
   __device__ __forceinline__ int k(int r) const { return r - r_first; }
   __device__ __forceinline__ const R* frow(int r) const { return fs + (k(r) % NF) * SM::ROW; }
@@ -120,31 +125,22 @@ struct AdjMarch {
     pr[4 * SM::PW + pi] = ir;
   }
 
-  // prep of row r: own column (prep index t+1) and, on lanes 0 and 1, the
-  // halo columns x0-2 (index 0) and x0+BX-1 (index BX+1)
+  // prep of row r: the thread's own column (box column t-2+HL, prep index t)
   __device__ __forceinline__ void prep(const AdjCoef<R>& a, int r) const {
-    const R* fr = frow(r);
-    const R* lr = lrow(r);
-    R* pr = prow(r);
-    prep_col(a, fr, lr, pr, x, r, SM::HL - 1 + t, t + 1);
-    if (t < 2) {
-      const int xc = (t == 0) ? x0 - 2 : x0 + BX - 1;
-      const int pi = (t == 0) ? 0 : BX + 1;
-      prep_col(a, fr, lr, pr, xc, r, xc - x0 + SM::HL, pi);
-    }
+    prep_col(a, frow(r), lrow(r), prow(r), x, r, SM::HL - 2 + t, t);
   }
 
   // lambda~ of output node (x, j); the rate gradients of the node go to G
   __device__ __forceinline__ void core(const AdjCoef<R>& a, int j, R G[16]) const {
     const Coef<R>& c = a.c;
-    const int bc = SM::HL - 1 + t;  // box column of x
+    const int bc = SM::HL - 2 + t;  // box column of x
     const R* pc = prow(j);
     const R* pn = prow(j + 1);
     const R* pp = prow(j - 1);
     const R* lc = lrow(j);
     const R* ln = lrow(j + 1);
     const R* lp_ = lrow(j - 1);
-    const int i1 = t + 1;  // prep index of x
+    const int i1 = t;  // prep index of x
     const R ux = pc[i1], uy = pc[SM::PW + i1];
     R lt[16];
 #pragma unroll
@@ -182,7 +178,7 @@ struct AdjMarch {
       const R uyb = c.inv2dx * (pc[G1 + i1 - 1] - pc[G1 + i1 + 1]) - c.inv2dy * (pp[G0 + i1] - pn[G0 + i1]);
       velocity_T(uxb, uyb, ux, uy, pc[4 * SM::PW + i1], lt);
     }
-    if (x <= L.nx) {
+    {
       R* o = out + L.node(x, j);
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q * L.plane] = lt[q];
@@ -192,7 +188,8 @@ struct AdjMarch {
   // Output rows [ja, jb) of the strip at x0 (a multiple of BX).  Returns
   // true if a wait expired (the CTA agreed to stop).
   __device__ __forceinline__ bool segment(const AdjCoef<R>& a, int ja, int jb, R G[16]) {
-    x = x0 - 1 + t;
+    x = x0 - 2 + t;
+    out_col = t >= 1 && t <= SM::SX && x <= L.nx;
     boxx = L.xoff + x0 - SM::HL;
     r_first = ja - 1;
     r_last = jb;
@@ -212,7 +209,7 @@ struct AdjMarch {
       if (!bad) prep(a, j + 1);
       if (__syncthreads_or(bad)) return true;
       refill(j - 1, j - 2);
-      core(a, j, G);
+      if (out_col) core(a, j, G);
     }
     return false;
   }
@@ -228,7 +225,7 @@ struct AdjMarch {
   }
 };
 
-// One CTA per (strip, row segment): strips x0 = blockIdx.x * BX, output
+// One CTA per (strip, row segment): strips x0 = blockIdx.x * SX, output
 // rows -1 + blockIdx.y * seglen ... (clipped at ny + 1).
 template <typename R, int BX, int NF, int NL>
 __global__ void __launch_bounds__(BX, 1)
@@ -253,7 +250,7 @@ __global__ void __launch_bounds__(BX, 1)
   m.out = out;
   m.L = L;
   m.t = threadIdx.x;
-  m.x0 = blockIdx.x * BX;
+  m.x0 = blockIdx.x * SM::SX;
   if (m.t == 0) {
     for (int s = 0; s < NF + NL; ++s) mbar_init(&m.fbar[s], 1);
     mbar_fence_init();
