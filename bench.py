@@ -2,7 +2,7 @@
 """Throughput of the MRT FD-LB step (arXiv:1106.0785) on GB300.
 
 Default workload: Richtmyer-Meshkov, 4096 x 1024 nodes, FP32 distributions
-with FP64 temperature recovery (a Mach-1.5 shock onto a cosine-perturbed
+with a compensated temperature numerator (a Mach-1.5 shock onto a cosine-perturbed
 light/heavy interface; seeded synthetic fields).  One bench step = one time
 step of the whole path: one fused step kernel (macroscopic recovery,
 velocity gradients, moments, equilibria, modified collision, Lax-Wendroff
@@ -162,7 +162,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("step_tiled.cu", "physics.cuh", "kernels.cuh"):
+    for name in ("step_tiled.cu", "march.cuh", "physics.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_1106_0785_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -374,7 +374,7 @@ def run_mine(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "richtmyer_meshkov_4096x1024", "nx": NX, "ny": NY,
-                   "precision": "fp32 storage, fp64 temperature recovery",
+                   "precision": "fp32 storage and arithmetic, compensated temperature numerator",
                    "l2": "inputs larger than L2 (268 MB per f copy)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": e2e,

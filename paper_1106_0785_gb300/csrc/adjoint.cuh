@@ -229,12 +229,7 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
   const R ir = R(1) / rho;
   const R T = (e - R(0.5) * (jx * ux + jy * uy)) * ir;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    R w = R(1);
-    if (vx_of(q) != 0) w -= c.lw[q][0] + c.lw[q][1];
-    if (vy_of(q) != 0) w -= c.lw[q][2] + c.lw[q][3];
-    lt[q] = w * lp[q];
-  }
+  for (int q = 0; q < 16; ++q) lt[q] = (R(1) - c.lwsum[q]) * lp[q];
   Harm<R> h;
   harmonics(g, h);
   R m[16], eq[16];

@@ -55,16 +55,9 @@ __global__ void __launch_bounds__(128) step_plain_kernel(const R* __restrict__ f
   R vout[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
-    const R fc = f[q];
-    R fn = fc - C[q];
-    if (vx_of(q) != 0) {
-      fn += c.lw[q][0] * (fin[q * P + E] - fc);
-      fn += c.lw[q][1] * (fin[q * P + W] - fc);
-    }
-    if (vy_of(q) != 0) {
-      fn += c.lw[q][2] * (fin[q * P + N] - fc);
-      fn += c.lw[q][3] * (fin[q * P + S] - fc);
-    }
+    const R fE = (vx_of(q) != 0) ? fin[q * P + E] : R(0), fW = (vx_of(q) != 0) ? fin[q * P + W] : R(0);
+    const R fN = (vy_of(q) != 0) ? fin[q * P + N] : R(0), fS = (vy_of(q) != 0) ? fin[q * P + S] : R(0);
+    const R fn = lw_update(c, q, f[q], C[q], fE, fW, fN, fS);
     fout[q * P + at] = fn;
     vout[q] = fn;
   }

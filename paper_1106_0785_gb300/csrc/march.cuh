@@ -190,16 +190,9 @@ struct March {
     R vout[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const R f0 = fc[q];
-      R v = f0 - C[q];
-      if (vx_of(q) != 0) {
-        v += c.lw[q][0] * (sc[q * SM::BW + SM::HL + t + 1] - f0);
-        v += c.lw[q][1] * (sc[q * SM::BW + SM::HL + t - 1] - f0);
-      }
-      if (vy_of(q) != 0) {
-        v += c.lw[q][2] * (fn[q] - f0);
-        v += c.lw[q][3] * (fp[q] - f0);
-      }
+      const R fE = (vx_of(q) != 0) ? sc[q * SM::BW + SM::HL + t + 1] : R(0);
+      const R fW = (vx_of(q) != 0) ? sc[q * SM::BW + SM::HL + t - 1] : R(0);
+      const R v = lw_update(c, q, fc[q], C[q], fE, fW, fn[q], fp[q]);
       if (active) out[q * plane] = v;
       vout[q] = v;
     }

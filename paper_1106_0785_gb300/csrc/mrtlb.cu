@@ -118,6 +118,22 @@ static int cuda_fail(mrtlb_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
   } while (0)
 
+// Round the four Lax-Wendroff weights of one velocity to multiples of a
+// power of two G >= 2^-mbits sum|k| (so that every weight and any partial
+// sum fits an mbits+1-bit significand) and return their sum, which is then
+// exact in that precision.  The change to each weight is at most G/2.
+static void on_common_grid(double k[4], int mbits, double* sum) {
+  double a = 0.0;
+  for (int i = 0; i < 4; ++i) a += std::fabs(k[i]);
+  *sum = 0.0;
+  if (a == 0.0) return;
+  const double G = std::ldexp(1.0, (int)std::ceil(std::log2(a)) - mbits);
+  for (int i = 0; i < 4; ++i) {
+    k[i] = std::nearbyint(k[i] / G) * G;
+    *sum += k[i];
+  }
+}
+
 static int build_coefficients(mrtlb_ctx* c) {
   const mrtlb_params& p = c->p;
   Coef<double>& k = c->c64;
@@ -135,6 +151,7 @@ static int build_coefficients(mrtlb_ctx* c) {
     k.lw[q][1] = bx + ax;  // west  (x - dx)
     k.lw[q][2] = by - ay;  // north (y + dy)
     k.lw[q][3] = by + ay;  // south (y - dy)
+    on_common_grid(k.lw[q], 52, &k.lwsum[q]);
   }
   for (int q = 0; q < 16; ++q) k.rate[q] = (q >= 4) ? p.dt * c->s[q] : 0.0;
   if (p.modified) {
@@ -192,7 +209,12 @@ static int build_coefficients(mrtlb_ctx* c) {
   f.a1x = (float)k.a1x; f.b1x = (float)k.b1x; f.a1y = (float)k.a1y; f.b1y = (float)k.b1y;
   f.inv2dx = (float)k.inv2dx; f.inv2dy = (float)k.inv2dy;
   for (int q = 0; q < 16; ++q)
-    for (int a = 0; a < 4; ++a) f.lw[q][a] = (float)k.lw[q][a];
+  for (int q = 0; q < 16; ++q) {
+    double w[4] = {k.lw[q][0], k.lw[q][1], k.lw[q][2], k.lw[q][3]}, sum;
+    on_common_grid(w, 23, &sum);
+    for (int a = 0; a < 4; ++a) f.lw[q][a] = (float)w[a];
+    f.lwsum[q] = (float)sum;
+  }
   for (int q = 0; q < 16; ++q) f.rate[q] = (float)k.rate[q];
   for (int q = 0; q < 4; ++q) f.mod[q] = (float)k.mod[q];
   for (int a = 0; a < 4; ++a)

@@ -46,6 +46,7 @@ struct Coef {
   // f_new = f + kE (f_E - f) + kW (f_W - f) + kN (f_N - f) + kS (f_S - f) - dt C,
   // kE = b_x - a_x, kW = b_x + a_x (a_x = v_x dt/2dx, b_x = (v_x dt/dx)^2/2), same in y
   R lw[16][4];
+  R lwsum[16];        // sum_n lw[q][n], exactly (the lw[q][n] lie on a common grid)
   R rate[16];         // dt * s_k (k >= 4 used)
   R mod[4];           // dt*(s7/s5-1), dt*(s7/s6-1), dt*(s8/s6-1), dt*(s8/s5-1)
   R invS[4][4];       // [shell A,B,C,D][family row: k=0,3,10,11]
@@ -123,10 +124,29 @@ MRTLB_HD void conserved(const R f[16], R& rho, R& jx, R& jy, R& e) {
 // T = (e rho - |j|^2 / 2) / rho^2.  The numerator, where the kinetic part
 // cancels against e behind strong shocks, is formed in FP64 from the exact
 // FP64 products of the FP32 moments; only the final scaling is FP32.
+#ifndef MRTLB_TEMP_COMPENSATED
+#define MRTLB_TEMP_COMPENSATED 1
+#endif
 __device__ __forceinline__ float temperature(float rho, float jx, float jy, float e, float inv_rho) {
+#if MRTLB_TEMP_COMPENSATED
+  // N = e rho - (jx^2 + jy^2)/2 in FP32 arithmetic to about twice FP32
+  // precision: each product split exactly into its rounded value and error
+  // (Dekker's TwoProduct in its fused multiply-add form), the two large
+  // cancellations done with Dekker's Fast2Sum, which is exact when the first
+  // operand is the larger; here e rho >= (jx^2 + jy^2)/2 whenever T >= 0.
+  const float p = e * rho, ep = fmaf(e, rho, -p);
+  const float hx = 0.5f * jx, hy = 0.5f * jy;  // exact
+  const float a = hx * jx, ea = fmaf(hx, jx, -a);
+  const float b = hy * jy, eb = fmaf(hy, jy, -b);
+  const float s1 = p - a, t1 = (p - s1) - a;
+  const float s2 = s1 - b, t2 = (s1 - s2) - b;
+  const float num = s2 + ((t1 + t2) + ((ep - ea) - eb));
+  return num * (inv_rho * inv_rho);
+#else
   const double j2 = fma((double)jy, (double)jy, (double)jx * (double)jx);
   const double num = fma((double)e, (double)rho, -0.5 * j2);
   return (float)num * (inv_rho * inv_rho);
+#endif
 }
 __device__ __forceinline__ double temperature(double rho, double jx, double jy, double e, double inv_rho) {
   const double j2 = fma(jy, jy, jx * jx);
@@ -142,6 +162,41 @@ __device__ __forceinline__ float recip(float x) {
   return r * fmaf(-x, r, 2.0f);
 }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+// One velocity's Lax-Wendroff update with the collision term,
+// f0 + sum_n k_qn (f_n - f0) - C, given the four neighbours' values.
+#ifndef MRTLB_LW_WEIGHTS
+#define MRTLB_LW_WEIGHTS 1
+#endif
+template <typename R>
+__device__ __forceinline__ R lw_update(const Coef<R>& c, int q, R f0, R Cq, R fE, R fW, R fN, R fS) {
+#if MRTLB_LW_WEIGHTS
+  // (1 - S) f0 - C + sum_n k_qn f_n with S = sum_n k_qn: summed over the
+  // nodes of a periodic grid this is sum f0 - sum C exactly whenever S is
+  // the exact sum of the stored k_qn, which the coefficient set-up ensures,
+  // so it conserves like the difference form with fewer operations.
+  R v = fma(-c.lwsum[q], f0, f0) - Cq;
+  if (vx_of(q) != 0) {
+    v = fma(c.lw[q][0], fE, v);
+    v = fma(c.lw[q][1], fW, v);
+  }
+  if (vy_of(q) != 0) {
+    v = fma(c.lw[q][2], fN, v);
+    v = fma(c.lw[q][3], fS, v);
+  }
+#else
+  R v = f0 - Cq;
+  if (vx_of(q) != 0) {
+    v += c.lw[q][0] * (fE - f0);
+    v += c.lw[q][1] * (fW - f0);
+  }
+  if (vy_of(q) != 0) {
+    v += c.lw[q][2] * (fN - f0);
+    v += c.lw[q][3] * (fS - f0);
+  }
+#endif
+  return v;
+}
+
 __device__ __forceinline__ float expr(float x) { return expf(x); }
 __device__ __forceinline__ double expr(double x) { return exp(x); }
 

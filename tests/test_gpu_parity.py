@@ -109,7 +109,7 @@ def test_fp64_init_equilibrium_matches_oracle(cuda):
 
 
 def test_fp32_smooth_flow_1000_steps(cuda):
-    """FP32 storage with FP64 temperature recovery vs the FP64 oracle."""
+    """FP32 storage and arithmetic (compensated temperature numerator) vs the FP64 oracle."""
     cfg = _cfg(160, 44, BCS["periodic"], "fp32", dt=1e-4)
     rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 40)
     p = oracle_params(cfg)
@@ -216,3 +216,57 @@ def test_tiled_and_plain_agree_fp32(cuda):
             res.append(sim.get_f())
     # two FP32 roundings of the same arithmetic, 50 steps apart from FMA contraction
     assert rel_plane_err(res[1], res[0]) < 1e-5
+
+
+def test_fp32_temperature_under_cancellation(cuda):
+    """Cold, fast FP32 states (mass on one or two velocities, a thin spread)
+    whose conserved moments are exact in FP32 (multiples of 2^-20 that sum
+    without rounding): T = (e rho - |j|^2/2) / rho^2 from the kernels must
+    match exact rational arithmetic to 1e-6.  A plain FP32 numerator loses
+    up to ~6e-5 here (e rho and |j|^2/2 cancel to about 1 part in 1e4)."""
+    from fractions import Fraction
+
+    from oracle import d2v16
+    V = d2v16.velocities().astype(int)
+    nx, ny = 64, 16
+    rng = np.random.default_rng(77)
+    n = rng.integers(0, 200, (ny, nx, 16))
+    for (j, i) in np.ndindex(ny, nx):
+        a, b = rng.integers(0, 16, 2)
+        n[j, i, a] += rng.integers(600000, 1000000)
+        n[j, i, b] += rng.integers(0, 2000)
+    f = np.moveaxis(n, 2, 0).astype(np.float32) * np.float32(2.0 ** -20)  # exact
+    cfg = M.Config(nx=nx, ny=ny, dx=0.01, dy=0.01, dt=1e-4, s=(0,) * 4 + (1e3,) * 12,
+                   bc=BCS["periodic"], precision="fp32")
+    with Simulation(cfg) as sim:
+        sim.set_f(f)
+        T = sim.macros()[3]
+    worst = 0.0
+    for (j, i) in np.ndindex(ny, nx):
+        fq = [Fraction(int(x), 2 ** 20) for x in n[j, i]]
+        rho = sum(fq)
+        jx = sum(x * int(v[0]) for x, v in zip(fq, V))
+        jy = sum(x * int(v[1]) for x, v in zip(fq, V))
+        e = sum(x * Fraction(int(v @ v), 2) for x, v in zip(fq, V))
+        Tex = (e * rho - (jx * jx + jy * jy) / 2) / rho ** 2
+        worst = max(worst, abs(T[j, i] / float(Tex) - 1))
+    assert worst < 1e-6, worst
+
+
+def test_fp32_conservation_drift(cuda):
+    """Periodic FP32 run, 4000 steps on the tiled kernel: the sums of
+    rho, j and e must not drift.  Both the Lax-Wendroff part (sum_n k_qn
+    stored with an exact sum) and the collision (no conserved components)
+    conserve exactly in exact arithmetic, so only unbiased rounding remains;
+    a systematic error in the stored weights of 1 ulp per step would move
+    the sums by ~1e-4 here."""
+    cfg = _cfg(512, 128, BCS["periodic"], "fp32", dt=1e-4)
+    rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 90)
+    with Simulation(cfg) as sim:
+        sim.set_kernel(M.MRTLB_KERNEL_TILED)
+        sim.init_equilibrium(rho, ux, uy, T)
+        a = sim.reduce()[:4]
+        sim.step(4000)
+        b = sim.reduce()[:4]
+    scale = np.array([a[0], a[0], a[0], a[3]])  # momenta relative to mass
+    assert np.all(np.abs(b - a) < 1e-6 * np.abs(scale)), (a, b)
