@@ -474,6 +474,11 @@ R* slot(const mrtlb_ctx* c, const mrtlb_adjoint_state* a, long n) {
   return (R*)((char*)a->seg + (size_t)n * c->state_bytes);
 }
 
+template <typename R>
+const Coef<R>& coef_of(const mrtlb_ctx* c) {
+  return *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&c->c32 : (const void*)&c->c64);
+}
+
 // Run the states of segment sg (t0 = sg S, len steps) through the slots:
 // slot n becomes B(f^{t0+n}) (walls refilled, ghosts written through by the
 // step that produced it).  Slot 0 must hold f^{t0}.  The last step writes
@@ -482,17 +487,12 @@ template <typename R>
 void run_segment(mrtlb_ctx* c, mrtlb_adjoint_state* a, long len, const Coef<R>& k, cudaStream_t st, R* last) {
   for (long n = 0; n < len; ++n) {
     R* fin = slot<R>(c, a, n);
-    launch_walls<R>(fin, c->L, c->c64, c->walls, st);
+    launch_walls<R>(fin, c->L, coef_of<R>(c), c->walls, st);
     R* fout = (n + 1 < len) ? slot<R>(c, a, n + 1) : last;
     if (!fout) break;
     if (a->tiled) launch_step_tiled<R>(a->plan[n], 0, c->L, k, c->err, st, fout);
     else launch_step_plain<R>(fin, fout, c->L, k, c->err, st);
   }
-}
-
-template <typename R>
-const Coef<R>& coef_of(const mrtlb_ctx* c) {
-  return *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&c->c32 : (const void*)&c->c64);
 }
 
 template <typename R>
@@ -510,7 +510,7 @@ int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, 
   ACK(cudaMemsetAsync(a->gacc, 0, 16 * sizeof(double), st), "clear");
   // seed on B(f^K)
   R* fK = (R*)c->f[c->cur];
-  launch_bc<R>(fK, L, c->c64, c->walls, st);
+  launch_bc<R>(fK, L, k, c->walls, st);
   dim3 gs((L.nx + 127) / 128, L.ny);
   if (dL_dmacros) adj_seed_macros_kernel<R><<<gs, 128, 0, st>>>(fK, dL_dmacros, lam0, L);
   if (dL_dfK) {  // a direct seed on the state (as mrtlb_get_f returns it); added to the macro seed

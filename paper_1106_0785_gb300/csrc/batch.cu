@@ -38,7 +38,8 @@ struct BatchInst {
 
 struct WallInst {
   Layout L;
-  Coef<double> c;
+  Coef<float> c32;   // the coefficients of the instance in both precisions
+  Coef<double> c64;
   Walls w;
   void* f[2];
   int first;  // index of this instance's first wall node in the flat enumeration
@@ -104,7 +105,8 @@ __global__ void walls_batched_kernel(const WallInst* __restrict__ wi, int nw, in
     else hi = mid - 1;
   }
   const WallInst& w = wi[lo];
-  wall_node<R>(reinterpret_cast<R*>(w.f[cur]), w.L, w.c, w.w, g - w.first);
+  const Coef<R>& c = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&w.c32 : (const void*)&w.c64);
+  wall_node<R>(reinterpret_cast<R*>(w.f[cur]), w.L, c, w.w, g - w.first);
 }
 
 // kernel variants by strip width
@@ -369,7 +371,8 @@ extern "C" int mrtlb_batch_create(mrtlb_ctx* const* ctxs, int n, mrtlb_batch** o
     WallInst e;
     std::memset(&e, 0, sizeof(e));
     e.L = b->ctx[i]->L;
-    e.c = b->ctx[i]->c64;
+    e.c32 = b->ctx[i]->c32;
+    e.c64 = b->ctx[i]->c64;
     e.w = b->ctx[i]->walls;
     e.f[0] = b->ctx[i]->f[0];
     e.f[1] = b->ctx[i]->f[1];

@@ -83,7 +83,7 @@ void launch_step_plain(const R* fin, R* fout, const Layout& L, const Coef<R>& c,
 // zero-gradient outflow; behind a wall a copy keeps the ghost finite).
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void bc_walls_kernel(R* f, Layout L, Coef<double> c, Walls w) {
+__global__ void bc_walls_kernel(R* f, Layout L, Coef<R> c, Walls w) {
   wall_node(f, L, c, w, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -112,16 +112,16 @@ __global__ void bc_ghost_kernel(R* f, Layout L) {
 }
 
 template <typename R>
-void launch_walls(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st) {
+void launch_walls(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStream_t st) {
   int nwall = 0;
   for (int s = 0; s < 4; ++s)
     if (L.bc[s] == BC_WALL) nwall += (s < 2) ? L.ny : L.nx;
-  if (nwall > 0) bc_walls_kernel<R><<<(nwall + 127) / 128, 128, 0, st>>>(f, L, c64, w);
+  if (nwall > 0) bc_walls_kernel<R><<<(nwall + 127) / 128, 128, 0, st>>>(f, L, c, w);
 }
 
 template <typename R>
-void launch_bc(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st) {
-  launch_walls<R>(f, L, c64, w, st);
+void launch_bc(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStream_t st) {
+  launch_walls<R>(f, L, c, w, st);
   const int n = (L.nx > L.ny) ? L.nx : L.ny;
   dim3 grd((n + 255) / 256, 16);
   bc_ghost_kernel<R><<<grd, 256, 0, st>>>(f, L);
@@ -277,8 +277,8 @@ void launch_reduce(const R* f, double* acc, double* Tprev, int have_prev, const 
 #define MRTLB_INSTANTIATE(R)                                                                     \
   template void launch_step_plain<R>(const R*, R*, const Layout&, const Coef<R>&, int*,          \
                                      cudaStream_t);                                              \
-  template void launch_bc<R>(R*, const Layout&, const Coef<double>&, const Walls&, cudaStream_t); \
-  template void launch_walls<R>(R*, const Layout&, const Coef<double>&, const Walls&, cudaStream_t); \
+  template void launch_bc<R>(R*, const Layout&, const Coef<R>&, const Walls&, cudaStream_t); \
+  template void launch_walls<R>(R*, const Layout&, const Coef<R>&, const Walls&, cudaStream_t); \
   template void launch_pack<R>(const R*, R*, const Layout&, cudaStream_t);                       \
   template void launch_unpack<R>(const R*, R*, const Layout&, cudaStream_t);                     \
   template void launch_init_eq<R>(const double*, const double*, const double*, const double*,    \

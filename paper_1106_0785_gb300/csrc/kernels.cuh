@@ -89,10 +89,9 @@ __host__ __device__ inline int wall_count(const Layout& L) {
 // Non-equilibrium extrapolation (Sec. IV A) of wall node number k (wall
 // nodes enumerated side by side: -x, +x, -y, +y): the wall node takes
 // f^eq(rho_a, u_w, T_w) + f_a - f^eq(rho_a, u_a, T_a) from its fluid
-// neighbour a, computed in FP64.
+// neighbour a, computed in the precision of the state.
 template <typename R>
-__device__ __forceinline__ void wall_node(R* f, const Layout& L, const Coef<double>& c, const Walls& w,
-                                          int k) {
+__device__ __forceinline__ void wall_node(R* f, const Layout& L, const Coef<R>& c, const Walls& w, int k) {
   int side = -1, i = 0, j = 0, ia = 0, ja = 0;
   for (int s = 0; s < 4 && side < 0; ++s) {
     const int n = (s < 2) ? L.ny : L.nx;
@@ -110,34 +109,34 @@ __device__ __forceinline__ void wall_node(R* f, const Layout& L, const Coef<doub
   if (side < 0) return;
   const long long P = L.plane;
   const long long a = L.node(ia, ja), at = L.node(i, j);
-  double g[16];
+  R g[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) g[q] = (double)f[q * P + a];
-  double rho, jx, jy, e;
+  for (int q = 0; q < 16; ++q) g[q] = f[q * P + a];
+  R rho, jx, jy, e;
   conserved(g, rho, jx, jy, e);
-  const double ir = 1.0 / rho;
-  const double ux = jx * ir, uy = jy * ir;
-  const double T = temperature(rho, jx, jy, e, ir);
-  double eqa[16], eqw[16], d[16], df[16];
+  const R ir = R(1) / rho;
+  const R ux = jx * ir, uy = jy * ir;
+  const R T = temperature(rho, jx, jy, e, ir);
+  R eqa[16], eqw[16], d[16], df[16];
   equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eqa);
-  const double uwx = w.ux[side], uwy = w.uy[side], Tw = w.T[side];
-  const double ew = rho * (Tw + 0.5 * (uwx * uwx + uwy * uwy));
+  const R uwx = (R)w.ux[side], uwy = (R)w.uy[side], Tw = (R)w.T[side];
+  const R ew = rho * (Tw + R(0.5) * (uwx * uwx + uwy * uwy));
   equilibrium(c, rho, ir, rho * uwx, rho * uwy, ew, uwx, uwy, Tw, eqw);
 #pragma unroll
   for (int q = 0; q < 16; ++q) d[q] = eqw[q] - eqa[q];
   inverse_full(c, d, df);
 #pragma unroll
-  for (int q = 0; q < 16; ++q) f[q * P + at] = (R)(g[q] + df[q]);
+  for (int q = 0; q < 16; ++q) f[q * P + at] = g[q] + df[q];
 }
 
 template <typename R>
 void launch_step_plain(const R* fin, R* fout, const Layout& L, const Coef<R>& c, int* err,
                        cudaStream_t st);
 template <typename R>
-void launch_bc(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st);
+void launch_bc(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStream_t st);
 // wall nodes only (the per-step fill; the step kernels keep the ghosts)
 template <typename R>
-void launch_walls(R* f, const Layout& L, const Coef<double>& c64, const Walls& w, cudaStream_t st);
+void launch_walls(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStream_t st);
 template <typename R>
 void launch_pack(const R* dense, R* padded, const Layout& L, cudaStream_t st);
 template <typename R>

@@ -385,7 +385,7 @@ static bool bound(mrtlb_ctx* c) { return c && c->f[0] && c->f[1]; }
 
 static void enqueue_bc(mrtlb_ctx* c, void* f) {
   if (c->prec == MRTLB_FP64) launch_bc<double>((double*)f, c->L, c->c64, c->walls, c->stream);
-  else launch_bc<float>((float*)f, c->L, c->c64, c->walls, c->stream);
+  else launch_bc<float>((float*)f, c->L, c->c32, c->walls, c->stream);
 }
 
 static int check_launch(mrtlb_ctx* c, const char* what) {
@@ -427,7 +427,7 @@ static void enqueue_one(mrtlb_ctx* c, int cur, cudaStream_t st, bool timed) {
   void* fout = c->f[cur ^ 1];
   // (ghosts of fin were written through by the previous step)
   if (c->prec == MRTLB_FP64) launch_walls<double>((double*)fin, c->L, c->c64, c->walls, st);
-  else launch_walls<float>((float*)fin, c->L, c->c64, c->walls, st);
+  else launch_walls<float>((float*)fin, c->L, c->c32, c->walls, st);
   if (timed) cudaEventRecord(c->ev[2 * c->ev_used], st);
   if (c->prec == MRTLB_FP64) {
     if (tiled) launch_step_tiled<double>(c->plan, cur, c->L, c->c64, c->err, st, fout);

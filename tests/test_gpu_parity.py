@@ -126,6 +126,24 @@ def test_fp32_smooth_flow_1000_steps(cuda):
     assert np.abs(a - ao).max() < 1e-5 * umax and np.abs(b - bo).max() < 1e-5 * umax
 
 
+@pytest.mark.parametrize("bc", ["walls_x", "walls_y"])
+def test_fp32_walls_300_steps(cuda, bc):
+    """FP32 with NEE walls (filled in FP32 each step) vs the FP64 oracle."""
+    cfg = _cfg(150, 37, BCS[bc], "fp32", dt=1e-4)
+    rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 45)
+    p = oracle_params(cfg)
+    f0 = fdlb.prepare(oeq.feq(rho, ux, uy, T), p)
+    with Simulation(cfg) as sim:
+        sim.set_f(f0.astype(np.float32))
+        sim.step(300)
+        r, a, b, t = sim.macros()
+    ro, ao, bo, to = fdlb.macros(fdlb.run(f0.astype(np.float32).astype(np.float64), p, 300))
+    assert np.abs(r / ro - 1).max() < 1e-5
+    assert np.abs(t / to - 1).max() < 1e-5
+    umax = max(np.abs(ao).max(), np.abs(bo).max())
+    assert np.abs(a - ao).max() < 1e-5 * umax and np.abs(b - bo).max() < 1e-5 * umax
+
+
 def test_fp32_across_shocks_l1(cuda):
     """Richtmyer-Meshkov set-up (shock + interface) on 512 x 128, 200 steps."""
     cfg, (rho, ux, uy, T) = workloads.richtmyer_meshkov(nx=512, ny=128, dt=1e-5)
