@@ -162,7 +162,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("step_tiled.cu", "march.cuh", "physics.cuh", "kernels.cuh"):
+    for name in ("step_tiled.cu", "march.cuh", "march_pair.cuh", "pair.cuh", "physics.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_1106_0785_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -312,7 +312,7 @@ def run_mine(args, world, rank, local):
     traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "step_tiled_kernel<float,128,4,4>", "kernel_ms_mean": kavg_s * 1e3,
+                "kernel": "step_pair_kernel<128,4,4>", "kernel_ms_mean": kavg_s * 1e3,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy)"}
 
     # ---- e2e through the C ABI with host buffers ---------------------------

@@ -15,6 +15,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -24,6 +25,7 @@
 
 #include "ctx.h"
 #include "march.cuh"
+#include "march_pair.cuh"
 
 namespace mrtlb {
 namespace {
@@ -94,6 +96,63 @@ __global__ void __launch_bounds__(BX, MINB) step_batched_kernel(const BatchInst<
   }
 }
 
+// FP32 with two nodes per thread (march_pair.cuh): BX/2 threads per CTA;
+// each tile's coefficients are expanded into pairs as they are copied.
+template <int BX, int NSLOT>
+__host__ __device__ constexpr size_t batch_pair_coef_off() {
+  return (PairSmem<BX, NSLOT>::bytes + 127) & ~(size_t)127;
+}
+template <int BX, int NSLOT>
+__host__ __device__ constexpr size_t batch_pair_smem() {
+  return batch_pair_coef_off<BX, NSLOT>() + sizeof(Coef<P2>);
+}
+
+template <int BX, int NSLOT, int MINB>
+__global__ void __launch_bounds__(BX / 2, MINB)
+    step_batched_pair_kernel(const BatchInst<float>* __restrict__ insts, const int4* __restrict__ tiles,
+                             int ntiles, int cur, int* err) {
+  using SM = PairSmem<BX, NSLOT>;
+  constexpr int NT = BX / 2;
+  constexpr int NF = (int)(offsetof(Coef<float>, version) / sizeof(float));  // float fields
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Coef<P2>* cs = reinterpret_cast<Coef<P2>*>(smem_raw + batch_pair_coef_off<BX, NSLOT>());
+  PairMarch<BX, NSLOT> m;
+  m.slots = reinterpret_cast<float*>(smem_raw);
+  m.U = reinterpret_cast<float*>(smem_raw + SM::u_off);
+  m.bars = reinterpret_cast<uint64_t*>(smem_raw + SM::bar_off);
+  m.err = err;
+  m.t = threadIdx.x;
+  m.kbase = 0;
+  if (m.t == 0) {
+    for (int s = 0; s < NSLOT; ++s) mbar_init(&m.bars[s], 1);
+    mbar_fence_init();
+  }
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const int4 tl = tiles[ti];  // (instance, x0, ja, jb)
+    const BatchInst<float>* in = insts + tl.x;
+    {
+      const float* src = &in->c.a1x;
+      P2* dst = &cs->a1x;
+      for (int k = m.t; k < NF; k += NT) dst[k] = P2(src[k]);
+      if (m.t == 0) {
+        cs->version = in->c.version;
+        cs->modified = in->c.modified;
+      }
+    }
+    m.L = in->L;
+    m.plane = m.L.plane;
+    m.map = &in->map[cur];
+    m.fout = in->f[cur ^ 1];
+    __syncthreads();  // coefficients in place (and the previous tile done with them)
+    if (m.segment(*cs, tl.y, tl.z, tl.w)) {
+      if (m.t == 0) atomicOr(err, ERRBIT_TIMEOUT);
+      m.drain();
+      return;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename R>
 __global__ void walls_batched_kernel(const WallInst* __restrict__ wi, int nw, int total, int cur) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -118,18 +177,32 @@ template <> struct BatchShapes<double> {
   static constexpr int NS = 4;
 };
 
+#ifndef MRTLB_PAIR
+#define MRTLB_PAIR 1
+#endif
+
 template <typename R, int BX, int MINB>
 void launch_batched_bx(const void* insts, const int4* tiles, int ntiles, int grid, int cur, int* err,
                        cudaStream_t st) {
   constexpr int NS = BatchShapes<R>::NS;
   static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(step_batched_kernel<R, BX, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)batch_smem<R, BX, NS>());
-    attr = true;
+  if constexpr (sizeof(R) == 4 && MRTLB_PAIR) {
+    if (!attr) {
+      cudaFuncSetAttribute(step_batched_pair_kernel<BX, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)batch_pair_smem<BX, NS>());
+      attr = true;
+    }
+    step_batched_pair_kernel<BX, NS, MINB><<<grid, BX / 2, batch_pair_smem<BX, NS>(), st>>>(
+        (const BatchInst<float>*)insts, tiles, ntiles, cur, err);
+  } else {
+    if (!attr) {
+      cudaFuncSetAttribute(step_batched_kernel<R, BX, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)batch_smem<R, BX, NS>());
+      attr = true;
+    }
+    step_batched_kernel<R, BX, NS, MINB><<<grid, BX, batch_smem<R, BX, NS>(), st>>>(
+        (const BatchInst<R>*)insts, tiles, ntiles, cur, err);
   }
-  step_batched_kernel<R, BX, NS, MINB><<<grid, BX, batch_smem<R, BX, NS>(), st>>>(
-      (const BatchInst<R>*)insts, tiles, ntiles, cur, err);
 }
 
 }  // namespace

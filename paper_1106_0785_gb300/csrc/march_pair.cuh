@@ -1,0 +1,182 @@
+// march_pair.cuh - the FP32 row march with two nodes per thread.
+//
+// Same pipeline as march.cuh (one CTA per strip of BX columns and a segment
+// of rows; each row arrives by one TMA box into an NSLOT ring with bounded
+// mbarrier waits), but thread t owns the adjacent columns x0 + 2t and
+// x0 + 2t + 1 and carries both nodes in packed FP32 pairs (pair.cuh), so
+// that every add, multiply and fused multiply-add of the per-node templates
+// serves two nodes, and shared-memory loads and global stores move 8 bytes.
+// Of the x-neighbours of the pair, the inner ones are the pair's own values
+// and the outer ones one 4-byte load each.  u of the two strip halo
+// columns comes from lanes 0 and 1.  A CTA has BX/2 threads.
+#pragma once
+
+#include <cuda.h>
+
+#include "march.cuh"
+
+namespace mrtlb {
+namespace {
+
+template <int BX, int NSLOT>
+struct PairSmem {
+  using S = Smem<float, BX, NSLOT>;  // the same TMA slots as the scalar march
+  static constexpr int HL = S::HL, BW = S::BW, SLOT = S::SLOT;
+  static constexpr int UW = BX + 4;          // u row: halo x0-1 at 1, column c at 2 + c, x0+BX at BX+2
+  static constexpr int UROW = 2 * UW;        // u_x row then u_y row
+  static constexpr size_t slot_bytes = S::slot_bytes;
+  static constexpr size_t u_off = (size_t)NSLOT * slot_bytes;
+  static constexpr size_t bar_off = (u_off + (size_t)4 * UROW * sizeof(float) + 15) & ~(size_t)15;
+  static constexpr size_t bytes = bar_off + NSLOT * sizeof(uint64_t);
+};
+
+template <int BX, int NSLOT>
+struct PairMarch {
+  using SM = PairSmem<BX, NSLOT>;
+  float* slots;
+  float* U;
+  uint64_t* bars;
+  const CUtensorMap* map;
+  float* fout;
+  int* err;
+  long long plane;
+  int t, x, boxx, r_first, r_last, issued_to, kbase;
+  bool act0, act1;
+  Layout L;
+
+  __device__ __forceinline__ int k(int r) const { return kbase + r - r_first; }
+  __device__ __forceinline__ const float* slot(int r) const {
+    return slots + (k(r) & (NSLOT - 1)) * SM::SLOT;
+  }
+  __device__ __forceinline__ float* urow(int r) const { return U + (k(r) & 3) * SM::UROW; }
+  __device__ __forceinline__ bool ready(int r) const {
+    return mbar_wait(&bars[k(r) & (NSLOT - 1)], (uint32_t)((k(r) / NSLOT) & 1));
+  }
+  __device__ __forceinline__ void issue(int r) {
+    const int s = k(r) & (NSLOT - 1);
+    mbar_expect_tx(&bars[s], (uint32_t)SM::slot_bytes);
+    tma_load_row(slots + s * SM::SLOT, map, boxx, r + 1, &bars[s]);
+  }
+  // the pair's own columns of row r, their macros, and u published to the ring
+  __device__ __forceinline__ void arrive(int r, P2 f[16], NodeMac<P2>& m) const {
+    const float* sl = slot(r);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) f[q] = P2(*reinterpret_cast<const float2*>(sl + q * SM::BW + SM::HL + 2 * t));
+    m = node_macros(f);
+    float* u = urow(r);
+    *reinterpret_cast<float2*>(u + 2 + 2 * t) = m.ux.v;
+    *reinterpret_cast<float2*>(u + SM::UW + 2 + 2 * t) = m.uy.v;
+    if (t < 2) {  // halo columns x0-1 (t = 0) and x0+BX (t = 1)
+      const int col = (t == 0) ? SM::HL - 1 : SM::HL + BX;
+      float g[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) g[q] = sl[q * SM::BW + col];
+      const NodeMac<float> mh = node_macros(g);
+      const int ui = (t == 0) ? 1 : BX + 2;
+      u[ui] = mh.ux;
+      u[SM::UW + ui] = mh.uy;
+    }
+  }
+  // one output row j for both columns; fp/fc hold rows j-1, j, fn receives
+  // row j+1.  Returns true if the CTA must stop (a wait expired).
+  __device__ __forceinline__ bool row(int j, const Coef<P2>& c, const P2 (&fp)[16], const P2 (&fc)[16],
+                                      P2 (&fn)[16], const NodeMac<P2>& mp, const NodeMac<P2>& mc,
+                                      NodeMac<P2>& mn) {
+    const bool bad = !ready(j + 1);
+    arrive(j + 1, fn, mn);
+    if (__syncthreads_or(bad)) return true;
+    if (t == 0 && issued_to < r_last) {
+      fence_proxy_async();
+      ++issued_to;
+      issue(issued_to);
+    }
+    const float* sc = slot(j);
+    const float* u = urow(j);
+    const int ui = 2 + 2 * t;  // ring index of column x
+    const P2 uxE(u[ui + 1], u[ui + 2]), uxW(u[ui - 1], u[ui]);
+    const P2 uyE(u[SM::UW + ui + 1], u[SM::UW + ui + 2]), uyW(u[SM::UW + ui - 1], u[SM::UW + ui]);
+    const P2 dux_dx = P2((uxE - uxW) * c.inv2dx), duy_dx = P2((uyE - uyW) * c.inv2dx);
+    const P2 dux_dy = P2((mn.ux - mp.ux) * c.inv2dy), duy_dy = P2((mn.uy - mp.uy) * c.inv2dy);
+    P2 C[16];
+    collision(c, fc, dux_dx, dux_dy, duy_dx, duy_dy, mc.rho, mc.ir, mc.jx, mc.jy, mc.e, mc.ux, mc.uy,
+              mc.T, C);
+    float* out = fout + L.node(x, j);
+    P2 vout[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int b = q * SM::BW + SM::HL + 2 * t;
+      const P2 fE = (vx_of(q) != 0) ? P2(fc[q].v.y, sc[b + 2]) : P2(0.0f);
+      const P2 fW = (vx_of(q) != 0) ? P2(sc[b - 1], fc[q].v.x) : P2(0.0f);
+      vout[q] = lw_update(c, q, fc[q], C[q], fE, fW, fn[q], fp[q]);
+    }
+    if (act0 && act1) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) *reinterpret_cast<float2*>(out + q * plane) = vout[q].v;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (act0) out[q * plane] = vout[q].v.x;
+        if (act1) out[q * plane + 1] = vout[q].v.y;
+      }
+    }
+    const GhostTargets g0 = ghost_targets(L, x, j), g1 = ghost_targets(L, x + 1, j);
+    if (act0 && g0.any()) {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = vout[q].v.x;
+      write_ghosts(g0, plane, v, out);
+    }
+    if (act1 && g1.any()) {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = vout[q].v.y;
+      write_ghosts(g1, plane, v, out + 1);
+    }
+    const bool bad0 = act0 && (!(mc.rho.v.x > 0.0f) || !(mc.T.v.x > 0.0f));
+    const bool bad1 = act1 && (!(mc.rho.v.y > 0.0f) || !(mc.T.v.y > 0.0f));
+    if (bad0 || bad1) atomicOr(err, ERRBIT_NONPHYSICAL);
+    return false;
+  }
+
+  // Advance rows [ja, jb) of the strip at x0 (a multiple of BX); as March.
+  __device__ __forceinline__ bool segment(const Coef<P2>& c, int x0, int ja, int jb) {
+    x = x0 + 2 * t;
+    act0 = x >= L.i0 && x < L.i1;
+    act1 = x + 1 >= L.i0 && x + 1 < L.i1;
+    boxx = L.xoff + x0 - SM::HL;
+    r_first = ja - 1;
+    r_last = jb;
+    if (t == 0)
+      for (int kk = 0; kk < NSLOT && r_first + kk <= r_last; ++kk) issue(r_first + kk);
+    issued_to = min(r_first + NSLOT - 1, r_last);
+
+    P2 F0[16], F1[16], F2[16];
+    NodeMac<P2> M0, M1, M2;
+    bool bad = !ready(r_first);
+    arrive(r_first, F0, M0);
+    bad |= !ready(ja);
+    arrive(ja, F1, M1);
+    bool stopped = __syncthreads_or(bad);
+    for (int j = ja; !stopped && j < jb; ++j) {
+      if ((stopped = row(j, c, F0, F1, F2, M0, M1, M2))) break;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        F0[q] = F1[q];
+        F1[q] = F2[q];
+      }
+      M0 = M1;
+      M1 = M2;
+    }
+    if (!stopped) kbase += r_last - r_first + 1;
+    return stopped;
+  }
+
+  __device__ __forceinline__ void drain() {
+    if (t == 0)
+      for (int r = max(r_first, issued_to - NSLOT + 1); r <= issued_to; ++r) (void)ready(r);
+    __syncthreads();
+  }
+};
+
+}  // namespace
+}  // namespace mrtlb

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pair.cuh"
+
 namespace mrtlb {
 
 // D2V16 (Fig. 1): order fixed by rows m2 = v_x and m3 = v_y of M.
@@ -162,6 +164,28 @@ __device__ __forceinline__ float recip(float x) {
   return r * fmaf(-x, r, 2.0f);
 }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+// The same three functions on a pair of nodes (pair.cuh): the reciprocal's
+// Newton-Raphson step and the compensated numerator run packed; the
+// hardware approximation and the exponential run per lane.
+__device__ __forceinline__ P2 recip(P2 x) {
+  float a, b;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(a) : "f"(x.v.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(b) : "f"(x.v.y));
+  const P2 r(a, b);
+  return P2(r * fma(-x, r, P2(2.0f)));
+}
+__device__ __forceinline__ P2 temperature(P2 rho, P2 jx, P2 jy, P2 e, P2 inv_rho) {
+  const P2 p = e * rho, ep = fma(e, rho, -p);
+  const P2 hx = P2(0.5f) * jx, hy = P2(0.5f) * jy;
+  const P2 a = hx * jx, ea = fma(hx, jx, -a);
+  const P2 b = hy * jy, eb = fma(hy, jy, -b);
+  const P2 s1 = p - a, t1 = (p - s1) - a;
+  const P2 s2 = s1 - b, t2 = (s1 - s2) - b;
+  const P2 num = s2 + ((t1 + t2) + ((ep - ea) - eb));
+  return P2(num * P2(inv_rho * inv_rho));
+}
+__device__ __forceinline__ P2 expr(P2 x) { return P2(expf(x.v.x), expf(x.v.y)); }
+
 // One velocity's Lax-Wendroff update with the collision term,
 // f0 + sum_n k_qn (f_n - f0) - C, given the four neighbours' values.
 #ifndef MRTLB_LW_WEIGHTS

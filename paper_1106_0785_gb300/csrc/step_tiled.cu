@@ -3,7 +3,10 @@
 // side of the march lives in march.cuh.
 #include <cuda.h>
 
+#include <cstddef>
+
 #include "march.cuh"
+#include "march_pair.cuh"
 #include "step_tiled.cuh"
 
 namespace mrtlb {
@@ -43,6 +46,38 @@ __global__ void __launch_bounds__(BX, MINB) step_tiled_kernel(const __grid_const
   }
 }
 
+// FP32 with two nodes per thread (march_pair.cuh): BX columns, BX/2 threads.
+template <int BX, int NSLOT, int MINB>
+__global__ void __launch_bounds__(BX / 2, MINB)
+    step_pair_kernel(const __grid_constant__ CUtensorMap tmap, float* __restrict__ fout, const Layout L,
+                     const __grid_constant__ Coef<P2> c, int* err, const int seglen) {
+  using SM = PairSmem<BX, NSLOT>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int ja = L.j0 + blockIdx.y * seglen;
+  const int jb = min(ja + seglen, L.j1);
+  if (ja >= jb) return;  // uniform over the CTA
+  PairMarch<BX, NSLOT> m;
+  m.slots = reinterpret_cast<float*>(smem_raw);
+  m.U = reinterpret_cast<float*>(smem_raw + SM::u_off);
+  m.bars = reinterpret_cast<uint64_t*>(smem_raw + SM::bar_off);
+  m.map = &tmap;
+  m.fout = fout;
+  m.err = err;
+  m.plane = L.plane;
+  m.L = L;
+  m.t = threadIdx.x;
+  m.kbase = 0;
+  if (m.t == 0) {
+    for (int s = 0; s < NSLOT; ++s) mbar_init(&m.bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (m.segment(c, blockIdx.x * BX, ja, jb)) {
+    if (m.t == 0) atomicOr(err, ERRBIT_TIMEOUT);
+    m.drain();
+  }
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -67,6 +102,27 @@ EncodeFn get_encode() {
 template <typename R> struct Tile;
 template <> struct Tile<float> { static constexpr int BX = 128, NSLOT = 4, MINB = 4; };
 template <> struct Tile<double> { static constexpr int BX = 64, NSLOT = 4, MINB = 1; };
+
+#ifndef MRTLB_PAIR
+#define MRTLB_PAIR 1
+#endif
+#ifndef MRTLB_PAIR_MINB
+#define MRTLB_PAIR_MINB 4
+#endif
+
+// The FP32 coefficient block with every constant in both lanes of a pair.
+Coef<P2> pair_coef(const Coef<float>& c) {
+  static_assert(offsetof(Coef<float>, version) % sizeof(float) == 0, "layout");
+  constexpr int n = (int)(offsetof(Coef<float>, version) / sizeof(float));
+  static_assert(offsetof(Coef<P2>, version) == n * sizeof(P2), "layout");
+  Coef<P2> p;
+  const float* src = &c.a1x;
+  P2* dst = &p.a1x;
+  for (int i = 0; i < n; ++i) dst[i] = P2(src[i]);
+  p.version = c.version;
+  p.modified = c.modified;
+  return p;
+}
 
 }  // namespace
 
@@ -151,17 +207,29 @@ template <typename R>
 void launch_step_tiled(const TiledPlan& plan, int cur, const Layout& L, const Coef<R>& c, int* err,
                        cudaStream_t st, void* fout) {
   constexpr int BX = Tile<R>::BX, NS = Tile<R>::NSLOT, MB = Tile<R>::MINB;
-  using SM = Smem<R, BX, NS>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(step_tiled_kernel<R, BX, NS, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)SM::bytes);
-    attr = true;
-  }
   if (L.i1 <= L.i0 || L.j1 <= L.j0) return;
   dim3 grd(plan.nstrips, plan.nseg);
-  step_tiled_kernel<R, BX, NS, MB><<<grd, BX, SM::bytes, st>>>(plan.map[cur], (R*)fout, L, c, err,
-                                                               plan.seglen);
+  if constexpr (sizeof(R) == 4 && MRTLB_PAIR) {
+    using SM = PairSmem<BX, NS>;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(step_pair_kernel<BX, NS, MRTLB_PAIR_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SM::bytes);
+      attr = true;
+    }
+    step_pair_kernel<BX, NS, MRTLB_PAIR_MINB><<<grd, BX / 2, SM::bytes, st>>>(
+        plan.map[cur], (float*)fout, L, pair_coef(reinterpret_cast<const Coef<float>&>(c)), err, plan.seglen);
+  } else {
+    using SM = Smem<R, BX, NS>;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(step_tiled_kernel<R, BX, NS, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SM::bytes);
+      attr = true;
+    }
+    step_tiled_kernel<R, BX, NS, MB><<<grd, BX, SM::bytes, st>>>(plan.map[cur], (R*)fout, L, c, err,
+                                                                 plan.seglen);
+  }
 }
 
 template void launch_step_tiled<float>(const TiledPlan&, int, const Layout&, const Coef<float>&, int*,
