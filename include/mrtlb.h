@@ -133,7 +133,15 @@ int mrtlb_macros(mrtlb_ctx* ctx, double* rho, double* ux, double* uy,
 int mrtlb_reduce(mrtlb_ctx* ctx, double out[5]);
 
 /* Copy the state out / in as dense [16][ny][nx] in the context precision
- * (float for MRTLB_FP32, double for MRTLB_FP64).  get_f synchronises. */
+ * (float for MRTLB_FP32, double for MRTLB_FP64).  Both synchronise when the
+ * buffer is on the host.
+ *
+ * Host buffers (on_device = 0) of mrtlb_macros, mrtlb_get_f and mrtlb_set_f
+ * are borrowed for the duration of the call.  Page-locked host memory that
+ * is mapped into the device's address space (e.g. cudaHostAlloc, or a
+ * PyTorch pinned tensor) is read or written by the kernels directly over the
+ * host link; any other host memory goes through a library-owned device
+ * staging buffer and one copy. */
 int mrtlb_get_f(mrtlb_ctx* ctx, void* f, int on_device);
 int mrtlb_set_f(mrtlb_ctx* ctx, const void* f, int on_device);
 

@@ -348,6 +348,19 @@ static int ensure_scratch(mrtlb_ctx* c) {
   return MRTLB_OK;
 }
 
+// The device address of a host buffer the GPU reaches directly (page-locked
+// memory mapped into the device's address space), else null: such buffers
+// are read or written by the kernels themselves over the host link, with
+// no staging copy.
+static void* mapped_host(const void* host) {
+  cudaPointerAttributes a;
+  if (!host || cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
+}
+
 static int ensure_staging(mrtlb_ctx* c, size_t bytes) {
   if (c->staging_bytes >= bytes) return MRTLB_OK;
   if (c->staging) {
@@ -519,7 +532,12 @@ extern "C" int mrtlb_macros(mrtlb_ctx* c, double* rho, double* ux, double* uy, d
   enqueue_bc(c, f);  // wall nodes follow the current neighbours
   double* d[4] = {rho, ux, uy, T};
   double* dd[4] = {rho, ux, uy, T};
+  bool direct = !on_device;
   if (!on_device) {
+    for (int k = 0; k < 4; ++k)
+      if (d[k] && !(dd[k] = (double*)mapped_host(d[k]))) direct = false;
+  }
+  if (!on_device && !direct) {
     int rc = ensure_staging(c, 4 * n * sizeof(double));
     if (rc) return rc;
     for (int k = 0; k < 4; ++k) dd[k] = d[k] ? (double*)c->staging + k * n : nullptr;
@@ -528,7 +546,7 @@ extern "C" int mrtlb_macros(mrtlb_ctx* c, double* rho, double* ux, double* uy, d
   else launch_macros<float>((const float*)f, dd[0], dd[1], dd[2], dd[3], c->L, c->stream);
   int rc = check_launch(c, "macros");
   if (rc) return rc;
-  if (!on_device)
+  if (!on_device && !direct)
     for (int k = 0; k < 4; ++k)
       if (d[k]) CK(cudaMemcpyAsync(d[k], dd[k], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy macros");
   return sync_and_check(c);
@@ -559,7 +577,10 @@ extern "C" int mrtlb_get_f(mrtlb_ctx* c, void* f, int on_device) {
   void* cur = c->f[c->cur];
   enqueue_bc(c, cur);
   void* dst = f;
-  if (!on_device) {
+  void* direct = on_device ? nullptr : mapped_host(f);
+  if (direct) {
+    dst = direct;
+  } else if (!on_device) {
     int rc = ensure_staging(c, bytes);
     if (rc) return rc;
     dst = c->staging;
@@ -568,7 +589,7 @@ extern "C" int mrtlb_get_f(mrtlb_ctx* c, void* f, int on_device) {
   else launch_unpack<float>((const float*)cur, (float*)dst, c->L, c->stream);
   int rc = check_launch(c, "get_f");
   if (rc) return rc;
-  if (!on_device) CK(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, c->stream), "copy f");
+  if (!on_device && !direct) CK(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, c->stream), "copy f");
   return sync_and_check(c);
 }
 
@@ -577,7 +598,10 @@ extern "C" int mrtlb_set_f(mrtlb_ctx* c, const void* f, int on_device) {
   if (!f) return fail(c, MRTLB_ERR_ARG, "f is NULL");
   const size_t bytes = (size_t)16 * c->L.nx * c->L.ny * c->esize;
   const void* src = f;
-  if (!on_device) {
+  const void* direct = on_device ? nullptr : mapped_host(f);
+  if (direct) {
+    src = direct;
+  } else if (!on_device) {
     int rc = ensure_staging(c, bytes);
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->staging, f, bytes, cudaMemcpyHostToDevice, c->stream), "copy f");
