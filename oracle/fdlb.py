@@ -36,6 +36,11 @@ Boundaries (one ghost layer, Sec. IV):
               fluid node, rho_w = rho_n (reading R10).  Wall nodes are not
               advanced by the step; they are refilled from the new adjacent
               row after it.
+  "inflow"    a fixed state (Sec. IV B, the shock-bubble's post-shock side):
+              ghost = f^eq(rho, u, T) of the side's state.
+  "reflect"   specular reflection (Sec. IV B, "reflection conditions"):
+              ghost = the first interior node with the velocity set mirrored
+              across the side (the normal component of every v_i negated).
 """
 from dataclasses import dataclass, field
 
@@ -47,14 +52,25 @@ from .equilibrium import conserved, feq, feq_hat, primitive
 PERIODIC = "periodic"
 OUTFLOW = "outflow"
 WALL = "wall"
+INFLOW = "inflow"
+REFLECT = "reflect"
 
 
 @dataclass
 class Side:
     kind: str = PERIODIC
-    ux: float = 0.0   # wall velocity (wall only)
+    ux: float = 0.0   # wall or inflow velocity
     uy: float = 0.0
-    T: float = 1.0    # wall temperature (wall only)
+    T: float = 1.0    # wall or inflow temperature
+    rho: float = 1.0  # inflow density
+
+
+def mirror_permutation(axis):
+    """perm[i] = the velocity index of v_i with component `axis` negated."""
+    v = d2v16.velocities()
+    w = v.copy()
+    w[:, axis] = -w[:, axis]
+    return np.array([int(np.flatnonzero((v == wi).all(axis=1))[0]) for wi in w])
 
 
 @dataclass
@@ -103,6 +119,19 @@ def _walls(f, p):
     return f
 
 
+def _edge_ghost(edge, side, axis, p):
+    """Ghost layer beside a non-periodic side from the adjacent edge layer
+    edge (16, n): outflow and walls copy it (behind a wall the ghost is never
+    read by an advanced node; the copy keeps it finite), reflect mirrors the
+    velocity set across the side, inflow holds f^eq of the side's state."""
+    if side.kind == REFLECT:
+        return edge[mirror_permutation(axis)]
+    if side.kind == INFLOW:
+        one = np.ones(edge.shape[1:])
+        return feq(side.rho * one, side.ux * one, side.uy * one, side.T * one, p.version).astype(edge.dtype)
+    return edge.copy()
+
+
 def _ghosts(f, p):
     """f padded with one ghost node on every side: shape (16, ny+2, nx+2)."""
     nq, ny, nx = f.shape
@@ -114,16 +143,14 @@ def _ghosts(f, p):
         g[:, 1:-1, 0] = f[:, :, nx - 1]
         g[:, 1:-1, nx + 1] = f[:, :, 0]
     else:
-        # outflow: zero gradient; behind a wall the ghost is never read by
-        # an advanced node, a copy keeps it finite
-        g[:, 1:-1, 0] = f[:, :, 0]
-        g[:, 1:-1, nx + 1] = f[:, :, nx - 1]
+        g[:, 1:-1, 0] = _edge_ghost(f[:, :, 0], xm, 0, p)
+        g[:, 1:-1, nx + 1] = _edge_ghost(f[:, :, nx - 1], xp, 0, p)
     if ym.kind == PERIODIC:
         g[:, 0, 1:-1] = f[:, ny - 1, :]
         g[:, ny + 1, 1:-1] = f[:, 0, :]
     else:
-        g[:, 0, 1:-1] = f[:, 0, :]
-        g[:, ny + 1, 1:-1] = f[:, ny - 1, :]
+        g[:, 0, 1:-1] = _edge_ghost(f[:, 0, :], ym, 1, p)
+        g[:, ny + 1, 1:-1] = _edge_ghost(f[:, ny - 1, :], yp, 1, p)
     # corners are not part of the cross stencil; keep them finite
     g[:, 0, 0] = g[:, 1, 1]
     g[:, 0, -1] = g[:, 1, -2]
