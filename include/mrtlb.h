@@ -56,15 +56,21 @@ typedef enum {
 typedef enum {
   MRTLB_BC_PERIODIC = 0,  /* ghost = opposite edge (Sec. IV A, IV B) */
   MRTLB_BC_OUTFLOW = 1,   /* zero-gradient extrapolation (Sec. IV B) */
-  MRTLB_BC_WALL_NEE = 2   /* non-equilibrium extrapolation wall (Sec. IV A) */
+  MRTLB_BC_WALL_NEE = 2,  /* non-equilibrium extrapolation wall (Sec. IV A) */
+  MRTLB_BC_INFLOW = 3,    /* fixed state: ghost = f^eq(rho, u, T) of the side
+                             (the shock-bubble's post-shock side, Sec. IV B) */
+  MRTLB_BC_REFLECT = 4    /* specular reflection: ghost = the edge node with
+                             the velocity set mirrored across the side (Sec.
+                             IV B, "reflection conditions") */
 } mrtlb_bc_kind;
 
 typedef enum { MRTLB_FP32 = 0, MRTLB_FP64 = 1 } mrtlb_precision;
 
 typedef struct {
   int kind;        /* mrtlb_bc_kind */
-  double ux, uy;   /* wall velocity (MRTLB_BC_WALL_NEE only) */
-  double T;        /* wall temperature (MRTLB_BC_WALL_NEE only) */
+  double ux, uy;   /* wall or inflow velocity (MRTLB_BC_WALL_NEE, MRTLB_BC_INFLOW) */
+  double T;        /* wall or inflow temperature (> 0 there) */
+  double rho;      /* inflow density (MRTLB_BC_INFLOW only; > 0) */
 } mrtlb_bc;
 
 typedef struct {
@@ -83,8 +89,9 @@ typedef struct {
   double dx, dy, dt; /* node spacings and time step */
   mrtlb_bc bc[4];    /* sides -x, +x, -y, +y; periodic sides come in pairs and
                         walls may sit on one axis only */
-  int precision;     /* MRTLB_FP32: f stored and advanced in FP32, temperature
-                        recovered in FP64; MRTLB_FP64: everything in FP64 */
+  int precision;     /* MRTLB_FP32: f stored and advanced in FP32, the
+                        temperature numerator compensated to about twice FP32
+                        precision; MRTLB_FP64: everything in FP64 */
   void* stream;      /* cudaStream_t to enqueue on; NULL = legacy default */
 } mrtlb_params;
 

@@ -175,7 +175,7 @@ template <> struct AdjTile<float> { static constexpr int BX = MRTLB_ADJ_BX, NF =
 template <> struct AdjTile<double> { static constexpr int BX = 64, NF = 3, NL = 4; };
 
 // B^T, ghosts: every edge node collects the adjoints of the ghost cells that
-// mirror it (plane q = blockIdx.y).  The ghost cells keep their values:
+// copy it (plane q = blockIdx.y); inflow ghosts do not depend on f.  The ghost cells keep their values:
 // lambda is only ever read at advanced nodes, and every step overwrites
 // the whole padded grid [-1, nx] x [-1, ny].
 template <typename R>
@@ -194,11 +194,16 @@ __global__ void adj_ghosts_kernel(R* lam, Layout L) {
   if (t >= 2 * L.nx + L.ny && L.nx == 1) return;
   const GhostTargets g = ghost_targets(L, i, j);
   if (!g.any()) return;
-  R* p = lam + (long long)blockIdx.y * L.plane + L.node(i, j);
-  R v = *p;
-  for (int s = 0; s < 4; ++s)
-    if (g.w[s]) v += p[g.off[s]];
-  *p = v;
+  const int q = blockIdx.y;
+  R* p = lam + L.node(i, j);
+  R v = p[(long long)q * L.plane];
+  for (int s = 0; s < 4; ++s) {
+    if (!g.w[s]) continue;
+    // a reflecting side held plane q of the node in the mirrored plane
+    const int qg = g.mir[s] ? (s < 2 ? mirror_x(q) : mirror_y(q)) : q;
+    v += p[(long long)qg * L.plane + g.off[s]];
+  }
+  p[(long long)q * L.plane] = v;
 }
 
 // B^T, walls on one side: the wall node w was NEE(f(a)) of its fluid
@@ -575,6 +580,8 @@ int forward_impl(mrtlb_ctx* c, long K) {
       a->ckpt.push_back(p);
     }
   ACK(cudaMalloc(&a->seg, sb * (size_t)S), "cudaMalloc(segment)");
+  // the fixed inflow ghosts of every slot (a step writes the other ghosts)
+  for (long n = 0; n < S; ++n) launch_inflow<R>(slot<R>(c, a, n), c->L, coef_of<R>(c), c->walls, st);
   for (int b = 0; b < 2; ++b) ACK(cudaMalloc(&a->lam[b], sb), "cudaMalloc(lambda)");
   const size_t pb = (size_t)c->L.plane * c->esize;
   ACK(cudaMalloc(&a->gsh, pb), "cudaMalloc(gbar)");

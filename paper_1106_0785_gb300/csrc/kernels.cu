@@ -87,8 +87,32 @@ __global__ void bc_walls_kernel(R* f, Layout L, Coef<R> c, Walls w) {
   wall_node(f, L, c, w, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// f^eq of an inflow side's fixed state, plane q.
 template <typename R>
-__global__ void bc_ghost_kernel(R* f, Layout L) {
+__device__ __forceinline__ R inflow_value(const Coef<R>& c, const Walls& w, int side, int q) {
+  const R rho = (R)w.rho[side], ux = (R)w.ux[side], uy = (R)w.uy[side], T = (R)w.T[side];
+  const R ir = R(1) / rho;
+  R eq[16], fe[16];
+  equilibrium(c, rho, ir, rho * ux, rho * uy, rho * (T + R(0.5) * (ux * ux + uy * uy)), ux, uy, T, eq);
+  inverse_full(c, eq, fe);
+  return fe[q];
+}
+
+// One ghost value beside side s of a non-periodic side from the edge node
+// `edge` (plane-0 address): outflow and walls copy it, reflect takes the
+// mirrored plane, inflow the side's fixed equilibrium.
+template <typename R>
+__device__ __forceinline__ R side_ghost(const Coef<R>& c, const Walls& w, const Layout& L, int s, int q,
+                                        const R* edge) {
+  if (L.bc[s] == BC_INFLOW) return inflow_value(c, w, s, q);
+  if (L.bc[s] == BC_REFLECT) return edge[(long long)(s < 2 ? mirror_x(q) : mirror_y(q)) * L.plane];
+  return edge[(long long)q * L.plane];
+}
+
+// The ghost layer of f (plane q = blockIdx.y).  only_inflow: just the
+// inflow sides (buffers whose other ghosts the steps write).
+template <typename R>
+__global__ void bc_ghost_kernel(R* f, Layout L, Coef<R> c, Walls w, int only_inflow) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int q = blockIdx.y;
   const long long P = L.plane;
@@ -97,17 +121,29 @@ __global__ void bc_ghost_kernel(R* f, Layout L) {
     const int j = t;
     const long long row = (long long)(j + 1) * L.pitch;
     const long long first = row + L.xoff, last = row + L.xoff + L.nx - 1;
-    const bool per = (L.bc[0] == BC_PERIODIC);
-    fq[first - 1] = per ? fq[last] : fq[first];
-    fq[last + 1] = per ? fq[first] : fq[last];
+    if (L.bc[0] == BC_PERIODIC) {
+      if (!only_inflow) {
+        fq[first - 1] = fq[last];
+        fq[last + 1] = fq[first];
+      }
+    } else {
+      if (!only_inflow || L.bc[0] == BC_INFLOW) fq[first - 1] = side_ghost(c, w, L, 0, q, f + first);
+      if (!only_inflow || L.bc[1] == BC_INFLOW) fq[last + 1] = side_ghost(c, w, L, 1, q, f + last);
+    }
   }
   if (t < L.nx) {  // y sides, column i = t
     const int i = t;
     const long long first = (long long)1 * L.pitch + L.xoff + i;
     const long long last = (long long)L.ny * L.pitch + L.xoff + i;
-    const bool per = (L.bc[2] == BC_PERIODIC);
-    fq[first - L.pitch] = per ? fq[last] : fq[first];
-    fq[last + L.pitch] = per ? fq[first] : fq[last];
+    if (L.bc[2] == BC_PERIODIC) {
+      if (!only_inflow) {
+        fq[first - L.pitch] = fq[last];
+        fq[last + L.pitch] = fq[first];
+      }
+    } else {
+      if (!only_inflow || L.bc[2] == BC_INFLOW) fq[first - L.pitch] = side_ghost(c, w, L, 2, q, f + first);
+      if (!only_inflow || L.bc[3] == BC_INFLOW) fq[last + L.pitch] = side_ghost(c, w, L, 3, q, f + last);
+    }
   }
 }
 
@@ -124,7 +160,17 @@ void launch_bc(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStre
   launch_walls<R>(f, L, c, w, st);
   const int n = (L.nx > L.ny) ? L.nx : L.ny;
   dim3 grd((n + 255) / 256, 16);
-  bc_ghost_kernel<R><<<grd, 256, 0, st>>>(f, L);
+  bc_ghost_kernel<R><<<grd, 256, 0, st>>>(f, L, c, w, 0);
+}
+
+template <typename R>
+void launch_inflow(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStream_t st) {
+  bool any = false;
+  for (int s = 0; s < 4; ++s) any |= (L.bc[s] == BC_INFLOW);
+  if (!any) return;
+  const int n = (L.nx > L.ny) ? L.nx : L.ny;
+  dim3 grd((n + 255) / 256, 16);
+  bc_ghost_kernel<R><<<grd, 256, 0, st>>>(f, L, c, w, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -279,6 +325,7 @@ void launch_reduce(const R* f, double* acc, double* Tprev, int have_prev, const 
                                      cudaStream_t);                                              \
   template void launch_bc<R>(R*, const Layout&, const Coef<R>&, const Walls&, cudaStream_t); \
   template void launch_walls<R>(R*, const Layout&, const Coef<R>&, const Walls&, cudaStream_t); \
+  template void launch_inflow<R>(R*, const Layout&, const Coef<R>&, const Walls&, cudaStream_t); \
   template void launch_pack<R>(const R*, R*, const Layout&, cudaStream_t);                       \
   template void launch_unpack<R>(const R*, R*, const Layout&, cudaStream_t);                     \
   template void launch_init_eq<R>(const double*, const double*, const double*, const double*,    \

@@ -16,7 +16,22 @@
 
 namespace mrtlb {
 
-enum : int { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_WALL = 2 };
+enum : int { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_WALL = 2, BC_INFLOW = 3, BC_REFLECT = 4 };
+
+// The velocity index of v_q with its x (mirror_x) or y (mirror_y) component
+// negated: the plane a reflecting side maps q to.
+__host__ __device__ constexpr int mirror_x(int q) {
+  int m = q;
+  for (int p = 0; p < 16; ++p)
+    if (vx_of(p) == -vx_of(q) && vy_of(p) == vy_of(q)) m = p;
+  return m;
+}
+__host__ __device__ constexpr int mirror_y(int q) {
+  int m = q;
+  for (int p = 0; p < 16; ++p)
+    if (vx_of(p) == vx_of(q) && vy_of(p) == -vy_of(q)) m = p;
+  return m;
+}
 
 // Bits of the device error word.
 enum : int { ERRBIT_NONPHYSICAL = 1, ERRBIT_TIMEOUT = 2 };
@@ -34,12 +49,15 @@ struct Layout {
 };
 
 // Ghost cells that mirror an advanced edge node (x, j): periodic sides
-// mirror the opposite edge, zero-gradient outflow sides their own edge.
+// mirror the opposite edge, zero-gradient outflow and reflecting sides their
+// own edge (reflection with the velocity set mirrored across the side).
 // A step that writes these from the new values keeps the ghost layer of
 // f^{n+1} complete, so the next step needs no separate boundary launch.
-// Walls have no ghosts in use.  Offsets are relative to node (x, j).
+// Walls have no ghosts in use; inflow ghosts are constant, filled once in
+// every state buffer.  Offsets are relative to node (x, j).
 struct GhostTargets {
   bool w[4];
+  bool mir[4];  // reflecting side: plane q goes to the mirrored plane
   long long off[4];
   __device__ __forceinline__ bool any() const { return w[0] || w[1] || w[2] || w[3]; }
 };
@@ -47,11 +65,12 @@ struct GhostTargets {
 __device__ __forceinline__ GhostTargets ghost_targets(const Layout& L, int x, int j) {
   const bool xl = (x == 0), xr = (x == L.nx - 1), yl = (j == 0), yr = (j == L.ny - 1);
   GhostTargets g;
-  // ghost column -1 mirrors column 0 (outflow) or column nx-1 (periodic), etc.
-  g.w[0] = (xl && L.bc[0] == BC_OUTFLOW) || (xr && L.bc[0] == BC_PERIODIC);
-  g.w[1] = (xr && L.bc[1] == BC_OUTFLOW) || (xl && L.bc[1] == BC_PERIODIC);
-  g.w[2] = (yl && L.bc[2] == BC_OUTFLOW) || (yr && L.bc[2] == BC_PERIODIC);
-  g.w[3] = (yr && L.bc[3] == BC_OUTFLOW) || (yl && L.bc[3] == BC_PERIODIC);
+  // ghost column -1 holds column 0 (outflow, reflect) or column nx-1 (periodic), etc.
+  g.w[0] = (xl && (L.bc[0] == BC_OUTFLOW || L.bc[0] == BC_REFLECT)) || (xr && L.bc[0] == BC_PERIODIC);
+  g.w[1] = (xr && (L.bc[1] == BC_OUTFLOW || L.bc[1] == BC_REFLECT)) || (xl && L.bc[1] == BC_PERIODIC);
+  g.w[2] = (yl && (L.bc[2] == BC_OUTFLOW || L.bc[2] == BC_REFLECT)) || (yr && L.bc[2] == BC_PERIODIC);
+  g.w[3] = (yr && (L.bc[3] == BC_OUTFLOW || L.bc[3] == BC_REFLECT)) || (yl && L.bc[3] == BC_PERIODIC);
+  for (int s = 0; s < 4; ++s) g.mir[s] = (L.bc[s] == BC_REFLECT);
   g.off[0] = -(long long)x - 1;
   g.off[1] = (long long)(L.nx - x);
   g.off[2] = -(long long)(j + 1) * L.pitch;
@@ -67,15 +86,19 @@ __device__ __forceinline__ void write_ghosts(const GhostTargets& g, long long pl
   for (int s = 0; s < 4; ++s) {
     if (!g.w[s]) continue;
     R* p = out + g.off[s];
+    if (g.mir[s]) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) p[q * plane] = v[q];
+      for (int q = 0; q < 16; ++q) p[(s < 2 ? mirror_x(q) : mirror_y(q)) * plane] = v[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) p[q * plane] = v[q];
+    }
   }
 }
 
-
-
 struct Walls {
-  double ux[4], uy[4], T[4];  // per side
+  double ux[4], uy[4], T[4];  // per side: wall or inflow velocity and temperature
+  double rho[4];              // inflow density
 };
 
 // Number of wall nodes of a layout (NEE sides: ny nodes per x side, nx per y side).
@@ -134,6 +157,9 @@ void launch_step_plain(const R* fin, R* fout, const Layout& L, const Coef<R>& c,
                        cudaStream_t st);
 template <typename R>
 void launch_bc(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStream_t st);
+// the inflow sides' fixed ghosts only (state buffers a step writes into)
+template <typename R>
+void launch_inflow(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStream_t st);
 // wall nodes only (the per-step fill; the step kernels keep the ghosts)
 template <typename R>
 void launch_walls(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStream_t st);

@@ -261,7 +261,7 @@ extern "C" int mrtlb_create(const mrtlb_params* params, mrtlb_ctx** out) {
   if (p.eq_version < 1 || p.eq_version > 3) return fail(nullptr, MRTLB_ERR_ARG, "eq_version %d", p.eq_version);
   if (p.precision != MRTLB_FP32 && p.precision != MRTLB_FP64) return fail(nullptr, MRTLB_ERR_ARG, "precision %d", p.precision);
   for (int s = 0; s < 4; ++s)
-    if (p.bc[s].kind < 0 || p.bc[s].kind > 2) return fail(nullptr, MRTLB_ERR_ARG, "bc[%d].kind = %d", s, p.bc[s].kind);
+    if (p.bc[s].kind < 0 || p.bc[s].kind > 4) return fail(nullptr, MRTLB_ERR_ARG, "bc[%d].kind = %d", s, p.bc[s].kind);
   for (int a = 0; a < 2; ++a) {
     const int k0 = p.bc[2 * a].kind, k1 = p.bc[2 * a + 1].kind;
     if ((k0 == MRTLB_BC_PERIODIC) != (k1 == MRTLB_BC_PERIODIC))
@@ -272,9 +272,12 @@ extern "C" int mrtlb_create(const mrtlb_params* params, mrtlb_ctx** out) {
   if (xwall && ywall) return fail(nullptr, MRTLB_ERR_UNSUPPORTED, "walls on one axis only");
   if (xwall && p.nx < 3) return fail(nullptr, MRTLB_ERR_ARG, "walls along x need nx >= 3");
   if (ywall && p.ny < 3) return fail(nullptr, MRTLB_ERR_ARG, "walls along y need ny >= 3");
-  for (int s = 0; s < 4; ++s)
+  for (int s = 0; s < 4; ++s) {
     if (p.bc[s].kind == MRTLB_BC_WALL_NEE && !(p.bc[s].T > 0))
       return fail(nullptr, MRTLB_ERR_ARG, "wall temperature on side %d must be positive", s);
+    if (p.bc[s].kind == MRTLB_BC_INFLOW && (!(p.bc[s].T > 0) || !(p.bc[s].rho > 0)))
+      return fail(nullptr, MRTLB_ERR_ARG, "inflow density and temperature on side %d must be positive", s);
+  }
   // Lax-Wendroff stability: Courant number of the fastest axis speed (2)
   const double cfl = 2.0 * p.dt / (p.dx < p.dy ? p.dx : p.dy);
   if (cfl > 1.0) return fail(nullptr, MRTLB_ERR_ARG, "CFL number 2 dt / min(dx, dy) = %g exceeds 1", cfl);
@@ -321,6 +324,7 @@ extern "C" int mrtlb_create(const mrtlb_params* params, mrtlb_ctx** out) {
     c->walls.ux[s] = p.bc[s].ux;
     c->walls.uy[s] = p.bc[s].uy;
     c->walls.T[s] = p.bc[s].T;
+    c->walls.rho[s] = p.bc[s].rho;
   }
   c->state_bytes = (size_t)16 * (size_t)L.plane * c->esize;
   const int rc = build_coefficients(c);
@@ -396,9 +400,16 @@ extern "C" int mrtlb_bind(mrtlb_ctx* c, void* f_a, void* f_b, size_t bytes) {
 
 static bool bound(mrtlb_ctx* c) { return c && c->f[0] && c->f[1]; }
 
+// The boundary fill of f; the fixed inflow ghosts go into both state
+// buffers, since a step writes every other ghost of its output itself.
 static void enqueue_bc(mrtlb_ctx* c, void* f) {
   if (c->prec == MRTLB_FP64) launch_bc<double>((double*)f, c->L, c->c64, c->walls, c->stream);
   else launch_bc<float>((float*)f, c->L, c->c32, c->walls, c->stream);
+  for (int b = 0; b < 2; ++b) {
+    if (!c->f[b] || c->f[b] == f) continue;
+    if (c->prec == MRTLB_FP64) launch_inflow<double>((double*)c->f[b], c->L, c->c64, c->walls, c->stream);
+    else launch_inflow<float>((float*)c->f[b], c->L, c->c32, c->walls, c->stream);
+  }
 }
 
 static int check_launch(mrtlb_ctx* c, const char* what) {

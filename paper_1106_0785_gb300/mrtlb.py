@@ -27,6 +27,8 @@ MRTLB_ERR_STATE = -7
 MRTLB_BC_PERIODIC = 0
 MRTLB_BC_OUTFLOW = 1
 MRTLB_BC_WALL_NEE = 2
+MRTLB_BC_INFLOW = 3
+MRTLB_BC_REFLECT = 4
 
 MRTLB_FP32 = 0
 MRTLB_FP64 = 1
@@ -60,7 +62,7 @@ class MrtlbError(RuntimeError):
 
 class mrtlb_bc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("ux", ctypes.c_double),
-                ("uy", ctypes.c_double), ("T", ctypes.c_double)]
+                ("uy", ctypes.c_double), ("T", ctypes.c_double), ("rho", ctypes.c_double)]
 
 
 class mrtlb_params(ctypes.Structure):
@@ -359,7 +361,8 @@ def mrtlb_launches_per_step(ctx):
 # ----------------------------------------------------------------------------
 # Parameter marshalling
 # ----------------------------------------------------------------------------
-BC_NAMES = {"periodic": MRTLB_BC_PERIODIC, "outflow": MRTLB_BC_OUTFLOW, "wall": MRTLB_BC_WALL_NEE}
+BC_NAMES = {"periodic": MRTLB_BC_PERIODIC, "outflow": MRTLB_BC_OUTFLOW, "wall": MRTLB_BC_WALL_NEE,
+            "inflow": MRTLB_BC_INFLOW, "reflect": MRTLB_BC_REFLECT}
 
 
 @dataclass
@@ -374,7 +377,7 @@ class Config:
     Pr: float = 1.0
     s_visc: float = 0.0
     s_other: float = 0.0
-    # sides -x, +x, -y, +y: (kind, ux, uy, T)
+    # sides -x, +x, -y, +y: (kind, ux, uy, T) or, for inflow, (kind, ux, uy, T, rho)
     bc: tuple = field(default_factory=lambda: (("periodic", 0, 0, 1),) * 4)
     eq_version: int = 1
     modified: bool = True
@@ -404,7 +407,8 @@ class Config:
         p.dx, p.dy, p.dt = self.dx, self.dy, self.dt
         for k, side in enumerate(self.bc):
             kind = BC_NAMES[side[0]] if isinstance(side[0], str) else int(side[0])
-            p.bc[k] = mrtlb_bc(kind, float(side[1]), float(side[2]), float(side[3]))
+            rho = float(side[4]) if len(side) > 4 else 1.0
+            p.bc[k] = mrtlb_bc(kind, float(side[1]), float(side[2]), float(side[3]), rho)
         p.precision = MRTLB_FP64 if self.precision == "fp64" else MRTLB_FP32
         p.stream = stream
         p._keep = keep  # keep arrays alive while params are in use

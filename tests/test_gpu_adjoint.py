@@ -26,6 +26,8 @@ BCS = {
     "outflow_x": (("outflow", 0, 0, 1),) * 2 + (("periodic", 0, 0, 1),) * 2,
     "walls_y": (("periodic", 0, 0, 1),) * 2 + (("wall", 0.1, 0.0, 1.1), ("wall", 0.5, -0.05, 0.95)),
     "walls_x": (("wall", 0.02, 0.3, 1.0), ("wall", 0.0, -0.2, 1.2)) + (("outflow", 0, 0, 1),) * 2,
+    "reflect": (("reflect", 0, 0, 1),) * 2 + (("reflect", 0, 0, 1),) * 2,
+    "inflow": (("outflow", 0, 0, 1), ("inflow", -0.05, 0.02, 1.1, 1.2)) + (("reflect", 0, 0, 1),) * 2,
 }
 
 
@@ -36,9 +38,12 @@ def _cfg(nx, ny, bc, version=1, precision="fp64"):
                     eq_version=version, precision=precision)
 
 
+KINDS = {"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW, "wall": fdlb.WALL,
+         "inflow": fdlb.INFLOW, "reflect": fdlb.REFLECT}
+
+
 def _oracle_params(cfg, s=None):
-    sides = tuple(fdlb.Side({"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW, "wall": fdlb.WALL}[k], a, b, t)
-                  for k, a, b, t in cfg.bc)
+    sides = tuple(fdlb.Side(KINDS[side[0]], *side[1:]) for side in cfg.bc)
     p = fdlb.Params(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt, s=np.asarray(cfg.s),
                     sides=sides, version=cfg.eq_version, modified=cfg.modified)
     if s is not None:

@@ -23,11 +23,15 @@ pytestmark = pytest.mark.gpu
 KERNELS = {"plain": M.MRTLB_KERNEL_PLAIN, "tiled": M.MRTLB_KERNEL_TILED}
 
 
+KINDS = {"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW, "wall": fdlb.WALL,
+         "inflow": fdlb.INFLOW, "reflect": fdlb.REFLECT}
+
+
 def oracle_params(cfg):
     sides = []
-    for kind, ux, uy, T in cfg.bc:
-        sides.append(fdlb.Side({"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW,
-                                "wall": fdlb.WALL}[kind], ux, uy, T))
+    for side in cfg.bc:
+        kind, ux, uy, T = side[:4]
+        sides.append(fdlb.Side(KINDS[kind], ux, uy, T, *side[4:]))
     return fdlb.Params(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt,
                        s=np.asarray(cfg.s), sides=tuple(sides), version=cfg.eq_version,
                        modified=cfg.modified)
@@ -44,6 +48,10 @@ BCS = {
     "outflow_xy": (("outflow", 0, 0, 1),) * 4,
     "walls_y": (("periodic", 0, 0, 1),) * 2 + (("wall", 0.1, 0.0, 1.1), ("wall", 0.5, -0.05, 0.95)),
     "walls_x": (("wall", 0.02, 0.3, 1.0), ("wall", 0.0, -0.2, 1.2)) + (("outflow", 0, 0, 1),) * 2,
+    "reflect_y": (("periodic", 0, 0, 1),) * 2 + (("reflect", 0, 0, 1),) * 2,
+    "reflect_x": (("reflect", 0, 0, 1),) * 2 + (("outflow", 0, 0, 1),) * 2,
+    # the shock-bubble's sides: outflow left, fixed post-shock inflow right, reflecting top and bottom
+    "inflow": (("outflow", 0, 0, 1), ("inflow", -0.05, 0.02, 1.1, 1.2)) + (("reflect", 0, 0, 1),) * 2,
 }
 
 
@@ -126,9 +134,10 @@ def test_fp32_smooth_flow_1000_steps(cuda):
     assert np.abs(a - ao).max() < 1e-5 * umax and np.abs(b - bo).max() < 1e-5 * umax
 
 
-@pytest.mark.parametrize("bc", ["walls_x", "walls_y"])
-def test_fp32_walls_300_steps(cuda, bc):
-    """FP32 with NEE walls (filled in FP32 each step) vs the FP64 oracle."""
+@pytest.mark.parametrize("bc", ["walls_x", "walls_y", "reflect_y", "inflow"])
+def test_fp32_boundaries_300_steps(cuda, bc):
+    """FP32 with NEE walls (filled in FP32 each step), reflecting and inflow
+    sides vs the FP64 oracle."""
     cfg = _cfg(150, 37, BCS[bc], "fp32", dt=1e-4)
     rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 45)
     p = oracle_params(cfg)
