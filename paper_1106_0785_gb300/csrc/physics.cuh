@@ -187,9 +187,13 @@ __device__ __forceinline__ P2 temperature(P2 rho, P2 jx, P2 jy, P2 e, P2 inv_rho
 __device__ __forceinline__ P2 expr(P2 x) { return P2(expf(x.v.x), expf(x.v.y)); }
 
 // One velocity's Lax-Wendroff update with the collision term,
-// f0 + sum_n k_qn (f_n - f0) - C, given the four neighbours' values.
+// f0 + sum_n k_qn (f_n - f0) - C, given the four neighbours' values.  The
+// difference form keeps a uniform region exactly uniform (every f_n - f0
+// is an exact zero there); the fused form below (MRTLB_LW_WEIGHTS = 1) takes
+// fewer operations but makes the same rounding error at every node of a
+// uniform region, which then drifts by about one ulp per step.
 #ifndef MRTLB_LW_WEIGHTS
-#define MRTLB_LW_WEIGHTS 1
+#define MRTLB_LW_WEIGHTS 0
 #endif
 template <typename R>
 __device__ __forceinline__ R lw_update(const Coef<R>& c, int q, R f0, R Cq, R fE, R fW, R fN, R fS) {

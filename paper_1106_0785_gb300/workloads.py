@@ -14,6 +14,8 @@ Relaxation rates per workload (Pr = s7/s5 = s8/s6):
              sheared at U = 0.8 diverges within a few thousand steps for
              every time step tried)
   RM         s5..s8 = 1e4 (the paper's Fig. 7(b) pair), others 1e5
+  bubble     s5 = s6 in {1e4, 1e3}, s7 = s8 in {1e5, 1e4, 1e3}, others 1e5
+             (the six panels of Figs. 7 and 8)
 Initial jumps are tanh-smoothed (over 2 cells for Sod and the shock, 3 cells
 for the material interface): the central scheme rings a sharp jump into
 negative temperatures.
@@ -122,6 +124,41 @@ def richtmyer_meshkov(nx=4096, ny=1024, precision="fp32", dt=1e-5, mach=1.5,
 # ---------------------------------------------------------------------------
 # Random smooth fields for parity tests
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# Shock-bubble interaction (Sec. IV B, Figs. 7 and 8)
+# ---------------------------------------------------------------------------
+BUBBLE_PRE = (1.0, 0.0, 0.0, 1.0)            # (rho, u_x, u_y, p) ahead of the shock
+BUBBLE_POST = (1.28, -0.3774, 0.0, 1.6512)    # behind the Mach-1.22 shock, moving -x
+BUBBLE_GAS = (0.1358, 0.0, 0.0, 1.0)          # the light bubble, in pressure balance
+
+
+def shock_bubble(nx=600, ny=100, precision="fp32", dt=1e-5, d=0.003, s_visc=1e4, s_cond=1e4,
+                 s_other=1e5, radius=25.0, modified=True):
+    """A Mach-1.22 shock travelling in -x from the post-shock block
+    (node columns 500..nx-1, the paper's 501..600) onto a cylindrical light
+    bubble centred at node (449, (ny-1)/2) (the paper's (450, 50), on the
+    channel's midline) of `radius` nodes (the paper gives none).  Sides:
+    extrapolation (outflow) on the left, the fixed post-shock state on the
+    right, reflection on top and bottom.  Interfaces tanh-smoothed over 3
+    nodes, the shock over 2."""
+    rpost, upost, vpost, ppost = BUBBLE_POST
+    cfg = Config(nx=nx, ny=ny, dx=d, dy=d, dt=dt, s=rates(s_visc, s_cond, s_other),
+                 bc=(("outflow", 0, 0, 1), ("inflow", upost, vpost, ppost / rpost, rpost),
+                     ("reflect", 0, 0, 1), ("reflect", 0, 0, 1)),
+                 modified=modified, precision=precision)
+    ix = np.arange(nx, dtype=float)[None, :]
+    iy = np.arange(ny, dtype=float)[:, None]
+    dist = np.sqrt((ix - 449.0) ** 2 + (iy - 0.5 * (ny - 1)) ** 2)
+    wb = 1.0 - _smooth_step(dist, radius, 3.0)       # 1 inside the bubble
+    ws = _smooth_step(ix + 0.0 * iy, 499.5, 2.0)      # 1 behind the shock
+    fields = []
+    for k in range(4):
+        a = BUBBLE_PRE[k] + (BUBBLE_GAS[k] - BUBBLE_PRE[k]) * wb
+        fields.append(a + (BUBBLE_POST[k] - a) * ws)
+    rho, ux, uy, p = fields
+    return cfg, (rho, ux, uy, p / rho)
+
+
 def smooth_fields(nx, ny, seed, rho0=1.0, T0=1.0, amp=0.1, umax=0.3, modes=3):
     """Periodic low-mode random fields (rho, ux, uy, T)."""
     rng = np.random.default_rng(seed)

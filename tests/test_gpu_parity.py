@@ -322,3 +322,21 @@ def test_pinned_host_buffers_match_pageable(cuda):
     assert np.array_equal(back.numpy(), want_f)
     for o, w in zip(outs, want_m):
         assert np.array_equal(o.numpy(), w)
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_fp32_uniform_state_does_not_drift(cuda, kernel):
+    """A uniform FP32 state stays uniform and does not drift: every
+    neighbour difference is an exact zero, so only the collision's rounding
+    (of order eps^2 here) remains.  An update that rounds the same way at
+    every node would move rho by ~1e-5 over these 2000 steps."""
+    cfg = _cfg(256, 40, BCS["periodic"], "fp32", dt=1e-4)
+    one = np.ones((cfg.ny, cfg.nx))
+    with Simulation(cfg) as sim:
+        sim.set_kernel(KERNELS[kernel])
+        sim.init_equilibrium(one, 0.1 * one, -0.05 * one, one)
+        r0, a0, b0, t0 = sim.macros()
+        sim.step(2000)
+        r, a, b, t = sim.macros()
+    assert np.abs(r / r0 - 1).max() < 1e-6 and np.abs(t / t0 - 1).max() < 1e-6
+    assert np.abs(a - a0).max() < 1e-6 and np.abs(b - b0).max() < 1e-6
