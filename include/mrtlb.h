@@ -258,7 +258,7 @@ int mrtlb_get_rates(const mrtlb_ctx* ctx, double* s);
  * implemented: Lax-Wendroff advection, collision with the modified
  * energy-flux terms, NEE walls, periodic and outflow ghosts), for
  * gradients of a loss on the final state with respect to the initial state
- * and the relaxation rates.  Equilibrium versions 1 and 2.
+ * and the relaxation rates.  Equilibrium versions 1, 2 and 3.
  *
  * mrtlb_adjoint_forward(ctx, K): advances the context K steps from its
  *   current state f^0 (like mrtlb_step) and keeps what the backward pass

@@ -640,8 +640,6 @@ extern "C" int mrtlb_adjoint_forward(mrtlb_ctx* c, long K) {
   if (!c) return MRTLB_ERR_ARG;
   if (!c->f[0] || !c->f[1]) return afail(c, MRTLB_ERR_STATE, "bind state buffers first");
   if (K < 0) return afail(c, MRTLB_ERR_ARG, "K < 0");
-  if (c->p.eq_version == 3)
-    return afail(c, MRTLB_ERR_UNSUPPORTED, "the adjoint covers equilibrium versions 1 and 2");
   release(c->adj);
   c->adj = new mrtlb_adjoint_state();
   return (c->prec == MRTLB_FP64) ? forward_impl<double>(c, K) : forward_impl<float>(c, K);
@@ -670,8 +668,6 @@ extern "C" int mrtlb_equilibrium_adjoint(mrtlb_ctx* c, const double* dL_df, cons
                                          double* dL_drho, double* dL_dux, double* dL_duy, double* dL_dT) {
   if (!c || !dL_df || !rho || !ux || !uy || !T || !dL_drho || !dL_dux || !dL_duy || !dL_dT)
     return MRTLB_ERR_ARG;
-  if (c->p.eq_version == 3)
-    return afail(c, MRTLB_ERR_UNSUPPORTED, "the adjoint covers equilibrium versions 1 and 2");
   const long long n = (long long)c->L.nx * c->L.ny;
   eq_adjoint_kernel<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(dL_df, rho, ux, uy, T, dL_drho, dL_dux,
                                                                          dL_duy, dL_dT, n, c->c64);

@@ -135,6 +135,33 @@ __device__ __forceinline__ void equilibrium_T(const Coef<R>& c, const EqIn<R>& x
     g.ux += eqb[14] * x.rho * (A + R(10) * ux2) + eqb[15] * x.rho * uy * R(10) * ux;
     g.uy += -eqb[14] * x.rho * ux * R(10) * uy + eqb[15] * x.rho * (B - R(10) * uy2);
     g.T += R(10) * x.rho * (eqb[14] * ux - eqb[15] * uy);
+  } else if (c.version == 3) {
+    // rows 12, 15, 16 of M applied to f_M,q = rho/(2 pi T) exp(-|v_q - u|^2 / 2T):
+    // their adjoints go back through the harmonics to f_M, then through
+    // d f_M,q = f_M,q (drho / rho + (v_q - u).du / T + (|v_q - u|^2 / 2T^2 - 1/T) dT)
+    Harm<R> hb;
+    const R sw[4] = {R(1), R(-4), R(16), R(-64)};
+    const R xw[4] = {R(1), R(-4), R(32), R(-128)};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      hb.S[s] = eqb[11] * sw[s];
+      hb.X[s] = eqb[14] * xw[s];
+      hb.Y[s] = -eqb[15] * xw[s];
+    }
+    hb.Q[0] = hb.Q[1] = hb.P[0] = hb.P[1] = R(0);
+    R fmb[16];
+    harmonics_T(hb, fmb);
+    const R iT = R(1) / x.T;
+    const R pre = x.rho * iT * R(0.15915494309189533576888376337251);  // rho / (2 pi T)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const R dx = R(vx_of(q)) - ux, dy = R(vy_of(q)) - uy, d2 = dx * dx + dy * dy;
+      const R w = fmb[q] * pre * expr(R(-0.5) * iT * d2);
+      g.rho += w * x.ir;
+      g.ux += w * dx * iT;
+      g.uy += w * dy * iT;
+      g.T += w * (R(0.5) * d2 * iT * iT - iT);
+    }
   }
   // w, u2, p
   g.e += R(6) * wb;

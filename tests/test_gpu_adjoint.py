@@ -77,7 +77,7 @@ def _adjoint(cuda, cfg, f0, K, w=None, seed_macros=None, interval=None, kernel="
 
 @pytest.mark.parametrize("kernel", list(KERNELS))
 @pytest.mark.parametrize("bc", list(BCS))
-@pytest.mark.parametrize("version", [1, 2])
+@pytest.mark.parametrize("version", [1, 2, 3])
 def test_one_step_adjoint_dot_product(cuda, bc, version, kernel):
     cfg = _cfg(140, 21, BCS[bc], version)
     f0 = _state(cfg, 100)
@@ -136,9 +136,10 @@ def test_macro_seed(cuda, kernel):
     assert abs(dL - float((lam0 * v).sum())) < 1e-10 * np.abs(weights).sum()
 
 
-def test_equilibrium_adjoint(cuda):
+@pytest.mark.parametrize("version", [1, 2, 3])
+def test_equilibrium_adjoint(cuda, version):
     import torch
-    cfg = _cfg(50, 9, BCS["periodic"], version=2)
+    cfg = _cfg(50, 9, BCS["periodic"], version=version)
     rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 130)
     rng = np.random.default_rng(131)
     lam = rng.standard_normal((16, cfg.ny, cfg.nx))
@@ -147,7 +148,7 @@ def test_equilibrium_adjoint(cuda):
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(cuda)
         outs = sim.equilibrium_adjoint(t(lam), t(rho), t(ux), t(uy), t(T))
     rhs = sum(float((o.cpu().numpy() * di).sum()) for o, di in zip(outs, d))
-    jf = oeq.feq(rho + 1j * H * d[0], ux + 1j * H * d[1], uy + 1j * H * d[2], T + 1j * H * d[3], 2).imag / H
+    jf = oeq.feq(rho + 1j * H * d[0], ux + 1j * H * d[1], uy + 1j * H * d[2], T + 1j * H * d[3], version).imag / H
     lhs = float((lam * jf).sum())
     assert abs(lhs - rhs) < 1e-11 * np.abs(lam * jf).sum()
 
@@ -162,14 +163,6 @@ def test_fp32_adjoint_close_to_fp64(cuda, kernel):
     ds32, l32 = _adjoint(cuda, cfg32, f0.astype(np.float32), 5, w=w, kernel=kernel)
     assert np.abs(l32 - l64).max() < 1e-4 * np.abs(l64).max()
     assert np.allclose(ds32[4:], ds64[4:], rtol=1e-3, atol=1e-4 * np.abs(ds64).max())
-
-
-def test_adjoint_rejects_version_3(cuda):
-    cfg = _cfg(20, 5, BCS["periodic"], version=3)
-    with Simulation(cfg) as sim:
-        with pytest.raises(M.MrtlbError) as ei:
-            sim.adjoint_forward(2)
-        assert ei.value.code == M.MRTLB_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("interval", [2, 0])
