@@ -96,6 +96,10 @@ __global__ void __launch_bounds__(BX, MINB) step_batched_kernel(const BatchInst<
   }
 }
 
+#ifndef MRTLB_BATCH_PREFETCH
+#define MRTLB_BATCH_PREFETCH 1
+#endif
+
 // FP32 with two nodes per thread (march_pair.cuh): BX/2 threads per CTA;
 // each tile's coefficients are expanded into pairs as they are copied.
 template <int BX, int NSLOT>
@@ -143,12 +147,18 @@ __global__ void __launch_bounds__(BX / 2, MINB)
     m.plane = m.L.plane;
     m.map = &in->map[cur];
     m.fout = in->f[cur ^ 1];
+    if (MRTLB_BATCH_PREFETCH && ti + (int)gridDim.x < ntiles) {  // the next tile streams in behind this one
+      const int4 nt = tiles[ti + gridDim.x];
+      const BatchInst<float>* nin = insts + nt.x;
+      m.set_next(&nin->map[cur], nin->L.xoff + nt.y - SM::HL, nt.z, nt.w);
+    }
     __syncthreads();  // coefficients in place (and the previous tile done with them)
     if (m.segment(*cs, tl.y, tl.z, tl.w)) {
       if (m.t == 0) atomicOr(err, ERRBIT_TIMEOUT);
       m.drain();
       return;
     }
+    m.advance();
     __syncthreads();
   }
 }

@@ -41,8 +41,13 @@ struct PairMarch {
   int* err;
   long long plane;
   int t, x, boxx, r_first, r_last, issued_to, kbase;
+  int pre = 0;  // rows of this segment already issued while the previous one ran
   bool act0, act1;
   Layout L;
+  // the next segment (none unless set by the caller): its map, box column,
+  // rows, and how many of its rows are issued so far
+  const CUtensorMap* nmap = nullptr;
+  int nboxx = 0, n_first = 0, n_last = -1, n_issued = 0;
 
   __device__ __forceinline__ int k(int r) const { return kbase + r - r_first; }
   __device__ __forceinline__ const float* slot(int r) const {
@@ -52,10 +57,33 @@ struct PairMarch {
   __device__ __forceinline__ bool ready(int r) const {
     return mbar_wait(&bars[k(r) & (NSLOT - 1)], (uint32_t)((k(r) / NSLOT) & 1));
   }
-  __device__ __forceinline__ void issue(int r) {
-    const int s = k(r) & (NSLOT - 1);
+  __device__ __forceinline__ void issue_k(int kk, const CUtensorMap* m, int bx, int r) {
+    const int s = kk & (NSLOT - 1);
     mbar_expect_tx(&bars[s], (uint32_t)SM::slot_bytes);
-    tma_load_row(slots + s * SM::SLOT, map, boxx, r + 1, &bars[s]);
+    tma_load_row(slots + s * SM::SLOT, m, bx, r + 1, &bars[s]);
+  }
+  __device__ __forceinline__ void issue(int r) { issue_k(k(r), map, boxx, r); }
+  // thread 0, after a barrier: one row into the slot that just became free
+  __device__ __forceinline__ void refill() {
+    if (issued_to < r_last) {
+      fence_proxy_async();
+      ++issued_to;
+      issue(issued_to);
+    } else if (nmap && n_first + n_issued <= n_last) {
+      fence_proxy_async();
+      const int kk = kbase + (r_last - r_first + 1) + n_issued;
+      issue_k(kk, nmap, nboxx, n_first + n_issued);
+      ++n_issued;
+    }
+  }
+  // the next segment (tensor map, box column, output rows [ja, jb)), for
+  // refill(); call before segment()
+  __device__ __forceinline__ void set_next(const CUtensorMap* m, int box_x, int ja, int jb) {
+    nmap = m;
+    nboxx = box_x;
+    n_first = ja - 1;
+    n_last = jb;
+    n_issued = 0;
   }
   // the pair's own columns of row r, their macros, and u published to the ring
   __device__ __forceinline__ void arrive(int r, P2 f[16], NodeMac<P2>& m) const {
@@ -85,11 +113,7 @@ struct PairMarch {
     const bool bad = !ready(j + 1);
     arrive(j + 1, fn, mn);
     if (__syncthreads_or(bad)) return true;
-    if (t == 0 && issued_to < r_last) {
-      fence_proxy_async();
-      ++issued_to;
-      issue(issued_to);
-    }
+    if (t == 0) refill();
     const float* sc = slot(j);
     const float* u = urow(j);
     const int ui = 2 + 2 * t;  // ring index of column x
@@ -146,9 +170,13 @@ struct PairMarch {
     boxx = L.xoff + x0 - SM::HL;
     r_first = ja - 1;
     r_last = jb;
-    if (t == 0)
-      for (int kk = 0; kk < NSLOT && r_first + kk <= r_last; ++kk) issue(r_first + kk);
-    issued_to = min(r_first + NSLOT - 1, r_last);
+    // rows the previous segment already put in flight (pre of them); the
+    // slots were read through the generic proxy by the previous segment
+    if (t == 0) {
+      if (pre < NSLOT) fence_proxy_async();
+      for (int kk = pre; kk < NSLOT && r_first + kk <= r_last; ++kk) issue(r_first + kk);
+    }
+    issued_to = min(r_first + max(pre, NSLOT) - 1, r_last);
 
     P2 F0[16], F1[16], F2[16];
     NodeMac<P2> M0, M1, M2;
@@ -171,9 +199,21 @@ struct PairMarch {
     return stopped;
   }
 
+  // Hand the prefetched rows of the next segment over: call after segment()
+  // returned false and before the next segment() (with its L set).
+  __device__ __forceinline__ void advance() {
+    pre = nmap ? n_issued : 0;
+    nmap = nullptr;
+    n_issued = 0;
+  }
+
   __device__ __forceinline__ void drain() {
-    if (t == 0)
-      for (int r = max(r_first, issued_to - NSLOT + 1); r <= issued_to; ++r) (void)ready(r);
+    if (t == 0) {
+      // every copy in flight: the current segment's rows and any of the next
+      const int klast = (nmap && n_issued > 0) ? kbase + (r_last - r_first + 1) + n_issued - 1 : k(issued_to);
+      for (int kk = max(k(r_first), klast - NSLOT + 1); kk <= klast; ++kk)
+        (void)mbar_wait(&bars[kk & (NSLOT - 1)], (uint32_t)((kk / NSLOT) & 1));
+    }
     __syncthreads();
   }
 };
