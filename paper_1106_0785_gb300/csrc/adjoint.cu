@@ -340,6 +340,8 @@ struct mrtlb_adjoint_state {
   void* uy = nullptr;
   double* gacc = nullptr;
   int core_blocks = 1;       // resident blocks of the core kernel on the device
+  size_t bytes = 0;          // device memory held in states
+  int kernel = 0;            // the kernel choice the plans were made for
   // the fused adjoint march: read maps of every slot and of both lambdas
   bool march = false;
   std::vector<CUtensorMap> fmap;
@@ -557,29 +559,22 @@ int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, 
   return MRTLB_OK;
 }
 
+// Buffers, tensor maps and launch plans of an adjoint state with S slots
+// and nck checkpoints.
 template <typename R>
-int forward_impl(mrtlb_ctx* c, long K) {
-  mrtlb_adjoint_state* a = c->adj;
+int allocate(mrtlb_ctx* c, mrtlb_adjoint_state* a, long S, long nck) {
   const size_t sb = c->state_bytes;
   cudaStream_t st = c->stream;
   const bool fp64 = sizeof(R) == 8;
-  // segment length: every state when K + 2 states fit in half the free memory
-  long S = c->adj_interval;
-  if (S <= 0) {
-    size_t fr = 0, tot = 0;
-    cudaMemGetInfo(&fr, &tot);
-    S = ((size_t)(K + 2) * sb <= fr / 2) ? K : (long)std::ceil(std::sqrt((double)K));
+  a->S = S;
+  a->kernel = c->kernel;
+  for (long i = 0; i < nck; ++i) {
+    void* p = nullptr;
+    ACK(cudaMalloc(&p, sb), "cudaMalloc(checkpoint)");
+    a->ckpt.push_back(p);
   }
-  a->K = K;
-  a->S = S = std::max(1L, std::min(S, std::max(K, 1L)));
-  a->nseg = std::max(1L, (K + S - 1) / S);
-  if (a->nseg > 1)
-    for (long i = 0; i < a->nseg; ++i) {
-      void* p = nullptr;
-      ACK(cudaMalloc(&p, sb), "cudaMalloc(checkpoint)");
-      a->ckpt.push_back(p);
-    }
   ACK(cudaMalloc(&a->seg, sb * (size_t)S), "cudaMalloc(segment)");
+  a->bytes = sb * (size_t)(S + nck + 2);
   // the fixed inflow ghosts of every slot (a step writes the other ghosts)
   for (long n = 0; n < S; ++n) launch_inflow<R>(slot<R>(c, a, n), c->L, coef_of<R>(c), c->walls, st);
   for (int b = 0; b < 2; ++b) ACK(cudaMalloc(&a->lam[b], sb), "cudaMalloc(lambda)");
@@ -606,6 +601,37 @@ int forward_impl(mrtlb_ctx* c, long K) {
     }
   }
   a->march = a->tiled && plan_adj_march<R>(c, a);
+  return MRTLB_OK;
+}
+
+template <typename R>
+int forward_impl(mrtlb_ctx* c, long K) {
+  const size_t sb = c->state_bytes;
+  cudaStream_t st = c->stream;
+  mrtlb_adjoint_state* old = c->adj;
+  // segment length: every state when K + 2 states fit in half the free
+  // memory (the buffers of a previous forward pass count as free)
+  long S = c->adj_interval;
+  if (S <= 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    fr += old ? old->bytes : 0;
+    S = ((size_t)(K + 2) * sb <= fr / 2) ? K : (long)std::ceil(std::sqrt((double)K));
+  }
+  S = std::max(1L, std::min(S, std::max(K, 1L)));
+  const long nseg = std::max(1L, (K + S - 1) / S);
+  const long nck = (nseg > 1) ? nseg : 0;
+  // a previous pass of the same shape keeps its buffers and plans
+  mrtlb_adjoint_state* a = old;
+  if (!(old && old->S == S && (long)old->ckpt.size() >= nck && old->kernel == c->kernel)) {
+    release(old);
+    c->adj = a = new mrtlb_adjoint_state();
+    const int rc = allocate<R>(c, a, S, nck);
+    if (rc) return rc;
+  }
+  a->K = K;
+  a->nseg = nseg;
+  a->held = -1;
   // all segments but the last: checkpoint, then the context's own time loop
   for (long sg = 0; sg + 1 < a->nseg; ++sg) {
     ACK(cudaMemcpyAsync(a->ckpt[sg], c->f[c->cur], sb, cudaMemcpyDeviceToDevice, st), "store checkpoint");
@@ -640,8 +666,6 @@ extern "C" int mrtlb_adjoint_forward(mrtlb_ctx* c, long K) {
   if (!c) return MRTLB_ERR_ARG;
   if (!c->f[0] || !c->f[1]) return afail(c, MRTLB_ERR_STATE, "bind state buffers first");
   if (K < 0) return afail(c, MRTLB_ERR_ARG, "K < 0");
-  release(c->adj);
-  c->adj = new mrtlb_adjoint_state();
   return (c->prec == MRTLB_FP64) ? forward_impl<double>(c, K) : forward_impl<float>(c, K);
 }
 

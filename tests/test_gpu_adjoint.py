@@ -211,3 +211,30 @@ def test_march_matches_two_pass_on_a_ragged_grid(cuda):
     lp, lt = lp.cpu().numpy(), lt.cpu().numpy()
     assert np.abs(lp - lt).max() < 1e-5 * np.abs(lp).max()
     assert np.allclose(dp[4:], dt[4:], rtol=1e-4, atol=1e-6 * np.abs(dp).max())
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_repeated_passes_reuse_the_adjoint_state(cuda, kernel):
+    """A second forward pass of the same length reuses the stored states'
+    buffers and plans and gives the same adjoint; a pass of another length
+    re-plans and matches a fresh context."""
+    import torch
+    cfg = _cfg(300, 40, BCS["inflow"])
+    f0 = _state(cfg, 170)
+    w = torch.from_numpy(np.random.default_rng(171).standard_normal(f0.shape)).to(cuda)
+
+    def run(sim, K):
+        sim.set_f(f0)
+        sim.adjoint_forward(K)
+        return sim.adjoint_backward(dL_dfK=w)
+
+    with Simulation(cfg) as sim:
+        sim.set_kernel(KERNELS[kernel])
+        (d1, l1), (d2, l2), (d3, l3) = run(sim, 5), run(sim, 5), run(sim, 9)
+    with Simulation(cfg) as fresh:
+        fresh.set_kernel(KERNELS[kernel])
+        d4, l4 = run(fresh, 9)
+    assert np.array_equal(l1.cpu().numpy(), l2.cpu().numpy())
+    assert np.allclose(d1, d2, rtol=1e-12, atol=0)
+    assert np.array_equal(l3.cpu().numpy(), l4.cpu().numpy())
+    assert np.allclose(d3, d4, rtol=1e-12, atol=0)
