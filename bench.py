@@ -96,7 +96,8 @@ def max_over_ranks(x, world, device=None):
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+             "clocks.mem,clocks.max.mem")
 
     def __init__(self, gpu):
         self.gpu = gpu
@@ -127,7 +128,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, mem, mmax = [], None, set(), [], None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -138,14 +139,23 @@ class ClockSampler:
                 smax = float(parts[2])
             except ValueError:
                 continue
+            try:
+                mem.append(float(parts[9]))
+                mmax = float(parts[10])
+            except (ValueError, IndexError):
+                pass
             for nm, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
             return None
         sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        mem.sort()
+        out = {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
+               "samples": len(sm)}
+        if mem:
+            out.update(mem_mhz=mem[len(mem) // 2], mem_max_mhz=mmax)
+        return out
 
 
 # ---------------------------------------------------------------------------
