@@ -41,6 +41,12 @@ Boundaries (one ghost layer, Sec. IV):
   "reflect"   specular reflection (Sec. IV B, "reflection conditions"):
               ghost = the first interior node with the velocity set mirrored
               across the side (the normal component of every v_i negated).
+  "diffuse"   diffuse reflection (Sec. IV A): velocities entering the fluid
+              leave the wall with the equilibrium of the wall state,
+              ghost_i = rho_w f^eq_i(1, u_w, T_w); the others copy the edge
+              node.  rho_w is the density for which the Lax-Wendroff
+              update moves no mass across the side, so the scheme keeps
+              the total mass exactly (reading R25).
 """
 from dataclasses import dataclass, field
 
@@ -54,12 +60,13 @@ OUTFLOW = "outflow"
 WALL = "wall"
 INFLOW = "inflow"
 REFLECT = "reflect"
+DIFFUSE = "diffuse"
 
 
 @dataclass
 class Side:
     kind: str = PERIODIC
-    ux: float = 0.0   # wall or inflow velocity
+    ux: float = 0.0   # wall (NEE or diffuse) or inflow velocity
     uy: float = 0.0
     T: float = 1.0    # wall or inflow temperature
     rho: float = 1.0  # inflow density
@@ -119,11 +126,42 @@ def _walls(f, p):
     return f
 
 
-def _edge_ghost(edge, side, axis, p):
+def _lw_weights(p, axis):
+    """Per velocity: the Lax-Wendroff weights of the +e_axis and -e_axis
+    neighbours in a node's update (the b - a and b + a of the step)."""
+    v = d2v16.velocities()[:, axis].astype(float)
+    d = p.dx if axis == 0 else p.dy
+    a = v * p.dt / (2.0 * d)
+    b = 0.5 * (v * p.dt / d) ** 2
+    return b - a, b + a
+
+
+def _diffuse_ghost(edge, side, axis, sign, p):
+    """Diffuse-reflection ghost beside the edge layer edge (16, n); sign = -1
+    for the low side of the axis (ghost at -e_axis), +1 for the high side."""
+    kp, km = _lw_weights(p, axis)
+    # a: weight of the ghost in the edge node's update; b: weight of the edge
+    # node in the ghost position's update (the mass the edge hands across)
+    a, b = (km, kp) if sign < 0 else (kp, km)
+    vn = -sign * d2v16.velocities()[:, axis]          # component along the inward normal
+    entering = vn > 0
+    one = np.ones(edge.shape[1:])
+    e = feq(one, side.ux * one, side.uy * one, side.T * one, p.version)
+    num = (b[:, None] * edge).sum(0) - (a[~entering, None] * edge[~entering]).sum(0)
+    den = (a[entering, None] * e[entering]).sum(0)
+    g = edge.copy()
+    g[entering] = (num / den)[None, :] * e[entering]
+    return g
+
+
+def _edge_ghost(edge, side, axis, p, sign=-1):
     """Ghost layer beside a non-periodic side from the adjacent edge layer
     edge (16, n): outflow and walls copy it (behind a wall the ghost is never
     read by an advanced node; the copy keeps it finite), reflect mirrors the
-    velocity set across the side, inflow holds f^eq of the side's state."""
+    velocity set across the side, inflow holds f^eq of the side's state,
+    diffuse re-emits the wall equilibrium."""
+    if side.kind == DIFFUSE:
+        return _diffuse_ghost(edge, side, axis, sign, p).astype(edge.dtype)
     if side.kind == REFLECT:
         return edge[mirror_permutation(axis)]
     if side.kind == INFLOW:
@@ -143,14 +181,14 @@ def _ghosts(f, p):
         g[:, 1:-1, 0] = f[:, :, nx - 1]
         g[:, 1:-1, nx + 1] = f[:, :, 0]
     else:
-        g[:, 1:-1, 0] = _edge_ghost(f[:, :, 0], xm, 0, p)
-        g[:, 1:-1, nx + 1] = _edge_ghost(f[:, :, nx - 1], xp, 0, p)
+        g[:, 1:-1, 0] = _edge_ghost(f[:, :, 0], xm, 0, p, -1)
+        g[:, 1:-1, nx + 1] = _edge_ghost(f[:, :, nx - 1], xp, 0, p, +1)
     if ym.kind == PERIODIC:
         g[:, 0, 1:-1] = f[:, ny - 1, :]
         g[:, ny + 1, 1:-1] = f[:, 0, :]
     else:
-        g[:, 0, 1:-1] = _edge_ghost(f[:, 0, :], ym, 1, p)
-        g[:, ny + 1, 1:-1] = _edge_ghost(f[:, ny - 1, :], yp, 1, p)
+        g[:, 0, 1:-1] = _edge_ghost(f[:, 0, :], ym, 1, p, -1)
+        g[:, ny + 1, 1:-1] = _edge_ghost(f[:, ny - 1, :], yp, 1, p, +1)
     # corners are not part of the cross stencil; keep them finite
     g[:, 0, 0] = g[:, 1, 1]
     g[:, 0, -1] = g[:, 1, -2]

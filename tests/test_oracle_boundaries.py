@@ -85,3 +85,72 @@ def test_inflow_ghost_is_the_side_equilibrium():
     g = fdlb._ghosts(_smooth_state(nx, ny, 4), p)
     want = oeq.feq(np.array([2.0]), np.array([0.3]), np.array([-0.1]), np.array([0.9]))[:, 0]
     assert np.allclose(g[:, 1:-1, 0], want[:, None], rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# diffuse reflection (Sec. IV A)
+# ---------------------------------------------------------------------------
+def test_diffuse_wall_keeps_a_resting_equilibrium():
+    nx, ny = 6, 7
+    dif = fdlb.Side(fdlb.DIFFUSE, 0.0, 0.0, 1.2)
+    per = fdlb.Side(fdlb.PERIODIC)
+    p = _params(nx, ny, (per, per, dif, dif))
+    one = np.ones((ny, nx))
+    f0 = oeq.feq(1.3 * one, 0 * one, 0 * one, 1.2 * one)
+    f = fdlb.run(f0, p, 10)
+    assert np.abs(f - f0).max() < 1e-14 * np.abs(f0).max()
+
+
+def test_diffuse_walls_keep_the_total_mass():
+    """rho_w is chosen so that the Lax-Wendroff update moves no mass across
+    the wall: the total mass is exact while momentum and energy are not."""
+    for sides in ((fdlb.Side(), fdlb.Side(), fdlb.Side(fdlb.DIFFUSE, -0.2, 0.05, 1.0),
+                   fdlb.Side(fdlb.DIFFUSE, 0.2, 0.0, 1.1)),
+                  (fdlb.Side(fdlb.DIFFUSE, 0.0, -0.2, 0.9), fdlb.Side(fdlb.DIFFUSE, 0.0, 0.2, 1.0),
+                   fdlb.Side(), fdlb.Side())):
+        nx, ny = 9, 8
+        f = _smooth_state(nx, ny, 6)
+        p = _params(nx, ny, sides)
+        m0 = oeq.conserved(f)[0].sum()
+        g = fdlb.run(f, p, 20)
+        r, jx, jy, e = oeq.conserved(g)
+        assert abs(r.sum() - m0) < 1e-13 * m0
+        assert abs(e.sum() - oeq.conserved(f)[3].sum()) > 1e-10  # the walls exchange energy
+
+
+def _slip_couette_steady(ny=12, U=0.2, s_visc=100.0, dt=1e-6, iters=8):
+    """Newton on F(f) = (step(f) - f)/dt (complex-step Jacobian) for a
+    channel between diffuse walls normal to y moving at -U and +U."""
+    s = np.full(16, s_visc)
+    s[:4] = 0
+    d = 1.0 / ny
+    sides = (fdlb.Side(), fdlb.Side(), fdlb.Side(fdlb.DIFFUSE, -U, 0.0, 1.0), fdlb.Side(fdlb.DIFFUSE, U, 0.0, 1.0))
+    p = fdlb.Params(nx=1, ny=ny, dx=d, dy=d, dt=dt, s=s, sides=sides)
+    y = (np.arange(ny) + 0.5) * d
+    ux = U * (2 * y - 1)
+    one = np.ones_like(y)
+    f = oeq.feq(one[:, None], ux[:, None], 0 * ux[:, None], one[:, None])
+    n = f.size
+    for _ in range(iters):
+        G = ((fdlb.step(f, p) - f) / dt).ravel()
+        J = np.empty((n, n))
+        for c in range(n):
+            fc = f.astype(complex).ravel()
+            fc[c] += 1e-30j
+            J[:, c] = (fdlb.step(fc.reshape(f.shape), p).ravel().imag / 1e-30 - (np.arange(n) == c)) / dt
+        f = f + np.linalg.lstsq(J, -G, rcond=1e-12)[0].reshape(f.shape)
+    assert np.abs((fdlb.step(f, p) - f) / dt).max() < 1e-6
+    _, u, _, T = fdlb.macros(f)
+    return y, u[:, 0], T[:, 0]
+
+
+def test_diffuse_slip_couette_shows_slip_and_a_temperature_jump():
+    """Sec. IV A: with diffuse walls the fluid next to a wall lags the wall
+    (velocity slip) and is hotter than it (temperature jump, from viscous
+    heating); the profile is odd in u and even in T about the midline."""
+    y, u, T = _slip_couette_steady()
+    U = 0.2
+    assert 0 < u[-1] < U and -U < u[0] < 0            # slip at both walls
+    assert T[0] > 1.0 and T[-1] > 1.0                 # hotter than the walls
+    assert T[len(T) // 2] > T[0]                      # heated in the middle
+    assert np.allclose(u, -u[::-1], atol=1e-9) and np.allclose(T, T[::-1], atol=1e-9)
