@@ -59,16 +59,21 @@ typedef enum {
   MRTLB_BC_WALL_NEE = 2,  /* non-equilibrium extrapolation wall (Sec. IV A) */
   MRTLB_BC_INFLOW = 3,    /* fixed state: ghost = f^eq(rho, u, T) of the side
                              (the shock-bubble's post-shock side, Sec. IV B) */
-  MRTLB_BC_REFLECT = 4    /* specular reflection: ghost = the edge node with
+  MRTLB_BC_REFLECT = 4,   /* specular reflection: ghost = the edge node with
                              the velocity set mirrored across the side (Sec.
                              IV B, "reflection conditions") */
+  MRTLB_BC_DIFFUSE = 5    /* diffuse reflection (Sec. IV A): velocities entering
+                             the fluid leave the wall with rho_w f^eq(1, u_w,
+                             T_w), the others copy the edge node; rho_w makes
+                             the Lax-Wendroff update move no mass across the
+                             side.  Refilled before every step. */
 } mrtlb_bc_kind;
 
 typedef enum { MRTLB_FP32 = 0, MRTLB_FP64 = 1 } mrtlb_precision;
 
 typedef struct {
   int kind;        /* mrtlb_bc_kind */
-  double ux, uy;   /* wall or inflow velocity (MRTLB_BC_WALL_NEE, MRTLB_BC_INFLOW) */
+  double ux, uy;   /* wall or inflow velocity (MRTLB_BC_WALL_NEE, _INFLOW, _DIFFUSE) */
   double T;        /* wall or inflow temperature (> 0 there) */
   double rho;      /* inflow density (MRTLB_BC_INFLOW only; > 0) */
 } mrtlb_bc;

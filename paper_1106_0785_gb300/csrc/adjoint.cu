@@ -206,6 +206,42 @@ __global__ void adj_ghosts_kernel(R* lam, Layout L) {
   p[(long long)q * L.plane] = v;
 }
 
+// B^T, diffuse reflection on side s: the ghost beyond edge node e holds
+// g = P f(e) with P linear (diffuse_ghost), so lambda(e) += P^T lambda~(g):
+//   lambda(e)_q += [q not entering] lambda~_q + (b_q - [q not entering] a_q) / D * sum_{p entering} e_p lambda~_p.
+template <typename R>
+__global__ void adj_diffuse_kernel(R* lam, Layout L, Coef<R> c, Walls w, int side) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = (side < 2) ? L.ny : L.nx;
+  if (k >= n) return;
+  const int i = (side == 0) ? 0 : (side == 1) ? L.nx - 1 : k;
+  const int j = (side == 2) ? 0 : (side == 3) ? L.ny - 1 : k;
+  const long long off = (side == 0) ? -1 : (side == 1) ? 1 : (side == 2) ? -(long long)L.pitch : L.pitch;
+  R* le = lam + L.node(i, j);
+  const R* lg = le + off;
+  R e[16];
+  wall_equilibrium(c, (R)w.ux[side], (R)w.uy[side], (R)w.T[side], e);
+  R den = R(0), s_in = R(0);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    if (!entering<R>(side, q)) continue;
+    R a, b;
+    diffuse_weights(c, side, q, a, b);
+    den += a * e[q];
+    s_in += e[q] * lg[(long long)q * L.plane];
+  }
+  const R g = s_in / den;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    R a, b;
+    diffuse_weights(c, side, q, a, b);
+    const bool in = entering<R>(side, q);
+    R add = (b - (in ? R(0) : a)) * g;
+    if (!in) add += lg[(long long)q * L.plane];
+    le[(long long)q * L.plane] += add;
+  }
+}
+
 // B^T, walls on one side: the wall node w was NEE(f(a)) of its fluid
 // neighbour a: lambda(a) += (dNEE/df(a))^T lambda~(w), lambda(w) = 0.
 template <typename R>
@@ -439,11 +475,12 @@ void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, long n, int li, const Co
   }
   const int perim = 2 * L.nx + 2 * L.ny;
   adj_ghosts_kernel<R><<<dim3((perim + 127) / 128, 16), 128, 0, st>>>(lam_out, L);
-  for (int s = 0; s < 4; ++s)
-    if (L.bc[s] == BC_WALL) {
-      const int nn = (s < 2) ? L.ny : L.nx;
+  for (int s = 0; s < 4; ++s) {
+    const int nn = (s < 2) ? L.ny : L.nx;
+    if (L.bc[s] == BC_DIFFUSE) adj_diffuse_kernel<R><<<(nn + 127) / 128, 128, 0, st>>>(lam_out, L, k, c->walls, s);
+    if (L.bc[s] == BC_WALL)
       adj_walls_kernel<R><<<(nn + 127) / 128, 128, 0, st>>>(lam_out, ft, L, c->c64, c->walls, s);
-    }
+  }
 }
 
 // Maps and row segments of the adjoint march; false if it cannot run.

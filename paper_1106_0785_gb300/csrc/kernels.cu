@@ -109,8 +109,9 @@ __device__ __forceinline__ R side_ghost(const Coef<R>& c, const Walls& w, const 
   return edge[(long long)q * L.plane];
 }
 
-// The ghost layer of f (plane q = blockIdx.y).  only_inflow: just the
-// inflow sides (buffers whose other ghosts the steps write).
+// The ghost layer of f (plane q = blockIdx.y), diffuse sides excepted (the
+// wall pass fills those).  only_inflow: just the inflow sides (buffers whose
+// other ghosts the steps write).
 template <typename R>
 __global__ void bc_ghost_kernel(R* f, Layout L, Coef<R> c, Walls w, int only_inflow) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,8 +128,10 @@ __global__ void bc_ghost_kernel(R* f, Layout L, Coef<R> c, Walls w, int only_inf
         fq[last + 1] = fq[first];
       }
     } else {
-      if (!only_inflow || L.bc[0] == BC_INFLOW) fq[first - 1] = side_ghost(c, w, L, 0, q, f + first);
-      if (!only_inflow || L.bc[1] == BC_INFLOW) fq[last + 1] = side_ghost(c, w, L, 1, q, f + last);
+      if ((!only_inflow && L.bc[0] != BC_DIFFUSE) || L.bc[0] == BC_INFLOW)
+        fq[first - 1] = side_ghost(c, w, L, 0, q, f + first);
+      if ((!only_inflow && L.bc[1] != BC_DIFFUSE) || L.bc[1] == BC_INFLOW)
+        fq[last + 1] = side_ghost(c, w, L, 1, q, f + last);
     }
   }
   if (t < L.nx) {  // y sides, column i = t
@@ -141,17 +144,17 @@ __global__ void bc_ghost_kernel(R* f, Layout L, Coef<R> c, Walls w, int only_inf
         fq[last + L.pitch] = fq[first];
       }
     } else {
-      if (!only_inflow || L.bc[2] == BC_INFLOW) fq[first - L.pitch] = side_ghost(c, w, L, 2, q, f + first);
-      if (!only_inflow || L.bc[3] == BC_INFLOW) fq[last + L.pitch] = side_ghost(c, w, L, 3, q, f + last);
+      if ((!only_inflow && L.bc[2] != BC_DIFFUSE) || L.bc[2] == BC_INFLOW)
+        fq[first - L.pitch] = side_ghost(c, w, L, 2, q, f + first);
+      if ((!only_inflow && L.bc[3] != BC_DIFFUSE) || L.bc[3] == BC_INFLOW)
+        fq[last + L.pitch] = side_ghost(c, w, L, 3, q, f + last);
     }
   }
 }
 
 template <typename R>
 void launch_walls(R* f, const Layout& L, const Coef<R>& c, const Walls& w, cudaStream_t st) {
-  int nwall = 0;
-  for (int s = 0; s < 4; ++s)
-    if (L.bc[s] == BC_WALL) nwall += (s < 2) ? L.ny : L.nx;
+  const int nwall = wall_count(L);
   if (nwall > 0) bc_walls_kernel<R><<<(nwall + 127) / 128, 128, 0, st>>>(f, L, c, w);
 }
 

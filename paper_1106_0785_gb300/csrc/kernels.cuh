@@ -16,7 +16,7 @@
 
 namespace mrtlb {
 
-enum : int { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_WALL = 2, BC_INFLOW = 3, BC_REFLECT = 4 };
+enum : int { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_WALL = 2, BC_INFLOW = 3, BC_REFLECT = 4, BC_DIFFUSE = 5 };
 
 // The velocity index of v_q with its x (mirror_x) or y (mirror_y) component
 // negated: the plane a reflecting side maps q to.
@@ -101,24 +101,70 @@ struct Walls {
   double rho[4];              // inflow density
 };
 
-// Number of wall nodes of a layout (NEE sides: ny nodes per x side, nx per y side).
+// Boundary cells refilled before every step: NEE wall nodes (ny per x side,
+// nx per y side) and diffuse-reflection ghost cells (likewise).
+__host__ __device__ inline bool refilled_side(int kind) { return kind == BC_WALL || kind == BC_DIFFUSE; }
 __host__ __device__ inline int wall_count(const Layout& L) {
   int n = 0;
   for (int s = 0; s < 4; ++s)
-    if (L.bc[s] == BC_WALL) n += (s < 2) ? L.ny : L.nx;
+    if (refilled_side(L.bc[s])) n += (s < 2) ? L.ny : L.nx;
   return n;
 }
 
-// Non-equilibrium extrapolation (Sec. IV A) of wall node number k (wall
-// nodes enumerated side by side: -x, +x, -y, +y): the wall node takes
-// f^eq(rho_a, u_w, T_w) + f_a - f^eq(rho_a, u_a, T_a) from its fluid
-// neighbour a, computed in the precision of the state.
+// The wall state's equilibrium at unit density, plane q.
+template <typename R>
+__device__ __forceinline__ void wall_equilibrium(const Coef<R>& c, R ux, R uy, R T, R e[16]) {
+  R eq[16];
+  equilibrium(c, R(1), R(1), ux, uy, T + R(0.5) * (ux * ux + uy * uy), ux, uy, T, eq);
+  inverse_full(c, eq, e);
+}
+
+// Diffuse reflection beside edge node `edge` (plane-0 address) on side s:
+// the ghost holds rho_w e_q for velocities entering the fluid and the edge
+// value otherwise, rho_w such that the Lax-Wendroff update moves no mass
+// across the side: with a_q the ghost's weight in the edge node's update
+// and b_q the edge node's in the ghost position's,
+//   rho_w = (sum_q b_q f_q - sum_{q not entering} a_q f_q) / sum_{q entering} a_q e_q.
+template <typename R>
+__device__ __forceinline__ bool entering(int s, int q) {
+  return (s == 0) ? vx_of(q) > 0 : (s == 1) ? vx_of(q) < 0 : (s == 2) ? vy_of(q) > 0 : vy_of(q) < 0;
+}
+template <typename R>
+__device__ __forceinline__ void diffuse_weights(const Coef<R>& c, int s, int q, R& a, R& b) {
+  const int ga = (s == 0) ? 1 : (s == 1) ? 0 : (s == 2) ? 3 : 2;  // lw index of the ghost neighbour
+  a = c.lw[q][ga];
+  b = c.lw[q][ga ^ 1];
+}
+template <typename R>
+__device__ __forceinline__ void diffuse_ghost(const Coef<R>& c, const Walls& w, const Layout& L, int s,
+                                              const R* edge, R* ghost) {
+  R e[16], f[16];
+  wall_equilibrium(c, (R)w.ux[s], (R)w.uy[s], (R)w.T[s], e);
+  // the flux balance in FP64 from the weights the update uses: in FP32 its
+  // rounding would leak mass the same way at every step (e cancels out of
+  // the balance, so its own rounding does not)
+  double num = 0.0, den = 0.0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    f[q] = edge[(long long)q * L.plane];
+    R a, b;
+    diffuse_weights(c, s, q, a, b);
+    num += (double)b * (double)f[q];
+    if (entering<R>(s, q)) den += (double)a * (double)e[q];
+    else num -= (double)a * (double)f[q];
+  }
+  const double rw = num / den;
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    ghost[(long long)q * L.plane] = entering<R>(s, q) ? (R)(rw * (double)e[q]) : f[q];
+}
+
 template <typename R>
 __device__ __forceinline__ void wall_node(R* f, const Layout& L, const Coef<R>& c, const Walls& w, int k) {
   int side = -1, i = 0, j = 0, ia = 0, ja = 0;
   for (int s = 0; s < 4 && side < 0; ++s) {
     const int n = (s < 2) ? L.ny : L.nx;
-    if (L.bc[s] != BC_WALL) continue;
+    if (!refilled_side(L.bc[s])) continue;
     if (k < n) {
       side = s;
       if (s == 0) { i = 0; j = k; ia = 1; ja = k; }
@@ -130,6 +176,11 @@ __device__ __forceinline__ void wall_node(R* f, const Layout& L, const Coef<R>& 
     }
   }
   if (side < 0) return;
+  if (L.bc[side] == BC_DIFFUSE) {  // the ghost cell beyond edge node (i, j)
+    const long long off = (side == 0) ? -1 : (side == 1) ? 1 : (side == 2) ? -(long long)L.pitch : L.pitch;
+    diffuse_ghost(c, w, L, side, f + L.node(i, j), f + L.node(i, j) + off);
+    return;
+  }
   const long long P = L.plane;
   const long long a = L.node(ia, ja), at = L.node(i, j);
   R g[16];

@@ -261,7 +261,7 @@ extern "C" int mrtlb_create(const mrtlb_params* params, mrtlb_ctx** out) {
   if (p.eq_version < 1 || p.eq_version > 3) return fail(nullptr, MRTLB_ERR_ARG, "eq_version %d", p.eq_version);
   if (p.precision != MRTLB_FP32 && p.precision != MRTLB_FP64) return fail(nullptr, MRTLB_ERR_ARG, "precision %d", p.precision);
   for (int s = 0; s < 4; ++s)
-    if (p.bc[s].kind < 0 || p.bc[s].kind > 4) return fail(nullptr, MRTLB_ERR_ARG, "bc[%d].kind = %d", s, p.bc[s].kind);
+    if (p.bc[s].kind < 0 || p.bc[s].kind > 5) return fail(nullptr, MRTLB_ERR_ARG, "bc[%d].kind = %d", s, p.bc[s].kind);
   for (int a = 0; a < 2; ++a) {
     const int k0 = p.bc[2 * a].kind, k1 = p.bc[2 * a + 1].kind;
     if ((k0 == MRTLB_BC_PERIODIC) != (k1 == MRTLB_BC_PERIODIC))
@@ -275,6 +275,8 @@ extern "C" int mrtlb_create(const mrtlb_params* params, mrtlb_ctx** out) {
   for (int s = 0; s < 4; ++s) {
     if (p.bc[s].kind == MRTLB_BC_WALL_NEE && !(p.bc[s].T > 0))
       return fail(nullptr, MRTLB_ERR_ARG, "wall temperature on side %d must be positive", s);
+    if (p.bc[s].kind == MRTLB_BC_DIFFUSE && !(p.bc[s].T > 0))
+      return fail(nullptr, MRTLB_ERR_ARG, "diffuse wall temperature on side %d must be positive", s);
     if (p.bc[s].kind == MRTLB_BC_INFLOW && (!(p.bc[s].T > 0) || !(p.bc[s].rho > 0)))
       return fail(nullptr, MRTLB_ERR_ARG, "inflow density and temperature on side %d must be positive", s);
   }
@@ -693,7 +695,7 @@ extern "C" int mrtlb_launches_per_step(const mrtlb_ctx* c) {
   if (!c) return MRTLB_ERR_ARG;
   int n = 1;  // the step (it writes the ghost layer through)
   for (int s = 0; s < 4; ++s)
-    if (c->L.bc[s] == BC_WALL) { ++n; break; }  // + the wall fill
+    if (refilled_side(c->L.bc[s])) { ++n; break; }  // + the wall and diffuse-ghost fill
   return n;
 }
 

@@ -29,6 +29,7 @@ MRTLB_BC_OUTFLOW = 1
 MRTLB_BC_WALL_NEE = 2
 MRTLB_BC_INFLOW = 3
 MRTLB_BC_REFLECT = 4
+MRTLB_BC_DIFFUSE = 5
 
 MRTLB_FP32 = 0
 MRTLB_FP64 = 1
@@ -362,7 +363,7 @@ def mrtlb_launches_per_step(ctx):
 # Parameter marshalling
 # ----------------------------------------------------------------------------
 BC_NAMES = {"periodic": MRTLB_BC_PERIODIC, "outflow": MRTLB_BC_OUTFLOW, "wall": MRTLB_BC_WALL_NEE,
-            "inflow": MRTLB_BC_INFLOW, "reflect": MRTLB_BC_REFLECT}
+            "inflow": MRTLB_BC_INFLOW, "reflect": MRTLB_BC_REFLECT, "diffuse": MRTLB_BC_DIFFUSE}
 
 
 @dataclass

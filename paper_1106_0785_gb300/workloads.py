@@ -125,6 +125,25 @@ def richtmyer_meshkov(nx=4096, ny=1024, precision="fp32", dt=1e-5, mach=1.5,
 # Random smooth fields for parity tests
 # ---------------------------------------------------------------------------
 # ---------------------------------------------------------------------------
+# Slip Couette flow between diffuse-reflection walls (Sec. IV A, Fig. 3)
+# ---------------------------------------------------------------------------
+def slip_couette(nx=100, ny=5, precision="fp64", dt=1e-4, d=0.01, U=0.2, Tw=1.0, s_visc=1e2, s_cond=None,
+                 s_other=None, version=1):
+    """Walls on the x sides (the paper's left and right walls) moving along
+    y at -U (left) and +U (right), both at Tw, periodic in y; the fluid
+    starts at rest with rho = 1, T = 1.  The paper does not give the rates
+    (the slip grows with the Knudsen number); by default all non-conserved
+    rates equal s_visc (Pr = 1)."""
+    s_cond = s_visc if s_cond is None else s_cond
+    s_other = s_visc if s_other is None else s_other
+    cfg = Config(nx=nx, ny=ny, dx=d, dy=d, dt=dt, s=rates(s_visc, s_cond, s_other),
+                 bc=(("diffuse", 0.0, -U, Tw), ("diffuse", 0.0, U, Tw), ("periodic", 0, 0, 1), ("periodic", 0, 0, 1)),
+                 eq_version=version, precision=precision)
+    one = np.ones((ny, nx))
+    return cfg, (one.copy(), 0 * one, 0 * one, one.copy())
+
+
+# ---------------------------------------------------------------------------
 # Shock-bubble interaction (Sec. IV B, Figs. 7 and 8)
 # ---------------------------------------------------------------------------
 BUBBLE_PRE = (1.0, 0.0, 0.0, 1.0)            # (rho, u_x, u_y, p) ahead of the shock

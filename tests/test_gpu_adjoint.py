@@ -28,6 +28,7 @@ BCS = {
     "walls_x": (("wall", 0.02, 0.3, 1.0), ("wall", 0.0, -0.2, 1.2)) + (("outflow", 0, 0, 1),) * 2,
     "reflect": (("reflect", 0, 0, 1),) * 2 + (("reflect", 0, 0, 1),) * 2,
     "inflow": (("outflow", 0, 0, 1), ("inflow", -0.05, 0.02, 1.1, 1.2)) + (("reflect", 0, 0, 1),) * 2,
+    "diffuse": (("periodic", 0, 0, 1),) * 2 + (("diffuse", -0.1, 0.02, 1.0), ("diffuse", 0.1, 0.0, 1.1)),
 }
 
 
@@ -39,7 +40,7 @@ def _cfg(nx, ny, bc, version=1, precision="fp64"):
 
 
 KINDS = {"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW, "wall": fdlb.WALL,
-         "inflow": fdlb.INFLOW, "reflect": fdlb.REFLECT}
+         "inflow": fdlb.INFLOW, "reflect": fdlb.REFLECT, "diffuse": fdlb.DIFFUSE}
 
 
 def _oracle_params(cfg, s=None):

@@ -24,7 +24,7 @@ KERNELS = {"plain": M.MRTLB_KERNEL_PLAIN, "tiled": M.MRTLB_KERNEL_TILED}
 
 
 KINDS = {"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW, "wall": fdlb.WALL,
-         "inflow": fdlb.INFLOW, "reflect": fdlb.REFLECT}
+         "inflow": fdlb.INFLOW, "reflect": fdlb.REFLECT, "diffuse": fdlb.DIFFUSE}
 
 
 def oracle_params(cfg):
@@ -52,6 +52,8 @@ BCS = {
     "reflect_x": (("reflect", 0, 0, 1),) * 2 + (("outflow", 0, 0, 1),) * 2,
     # the shock-bubble's sides: outflow left, fixed post-shock inflow right, reflecting top and bottom
     "inflow": (("outflow", 0, 0, 1), ("inflow", -0.05, 0.02, 1.1, 1.2)) + (("reflect", 0, 0, 1),) * 2,
+    "diffuse_y": (("periodic", 0, 0, 1),) * 2 + (("diffuse", -0.1, 0.02, 1.0), ("diffuse", 0.1, 0.0, 1.1)),
+    "diffuse_x": (("diffuse", 0.0, -0.2, 0.95), ("diffuse", 0.03, 0.2, 1.0)) + (("periodic", 0, 0, 1),) * 2,
 }
 
 
@@ -134,7 +136,7 @@ def test_fp32_smooth_flow_1000_steps(cuda):
     assert np.abs(a - ao).max() < 1e-5 * umax and np.abs(b - bo).max() < 1e-5 * umax
 
 
-@pytest.mark.parametrize("bc", ["walls_x", "walls_y", "reflect_y", "inflow"])
+@pytest.mark.parametrize("bc", ["walls_x", "walls_y", "reflect_y", "inflow", "diffuse_x"])
 def test_fp32_boundaries_300_steps(cuda, bc):
     """FP32 with NEE walls (filled in FP32 each step), reflecting and inflow
     sides vs the FP64 oracle."""
