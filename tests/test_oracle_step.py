@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 from oracle import d2v16, fdlb
+from oracle.stability import amplification_matrix
 from oracle import equilibrium as eq
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -179,46 +180,6 @@ def _jacobian(p, f0):
     return J
 
 
-def _paper_G(p, rho, ux, uy, T, kx, ky):
-    """G_ij as printed in Sec. III, with the rows for moments 7 and 8 replaced
-    as for the modified collision; spatial derivatives of u in the
-    modification carry the central-difference symbol i sin(k d)/d."""
-    M = d2v16.moment_matrix()
-    Minv = d2v16.moment_matrix_inverse()
-    v = d2v16.velocities().astype(float)
-    s = p.s
-    G = np.zeros((16, 16), dtype=complex)
-    for i in range(16):
-        adv = 0.0
-        for a, k, d in ((0, kx, p.dx), (1, ky, p.dy)):
-            nu = v[i, a] * p.dt / d
-            adv += -nu / 2 * (np.exp(1j * k * d) - np.exp(-1j * k * d)) \
-                + 0.5 * nu ** 2 * (np.exp(1j * k * d) - 2 + np.exp(-1j * k * d))
-        G[i, i] = 1.0 + adv
-    # d f^eq_k / d f_j through (rho, j, e), by complex step on the equilibrium
-    f0 = eq.feq(np.array(rho), np.array(ux), np.array(uy), np.array(T))
-    Deq = np.zeros((16, 16))
-    for j in range(16):
-        fc = f0.astype(complex)
-        fc[j] += 1e-30j
-        r, jx, jy, e = eq.conserved(fc)
-        Deq[:, j] = eq.feq_hat(r, jx, jy, e, p.version).imag / 1e-30
-    S = np.diag(s)
-    G -= p.dt * Minv @ S @ (M - Deq)
-    if p.modified:
-        dux = (v[:, 0] - ux) / rho  # d u_x / d f_j
-        duy = (v[:, 1] - uy) / rho
-        Kx = 1j * np.sin(kx * p.dx) / p.dx
-        Ky = 1j * np.sin(ky * p.dy) / p.dy
-        rT = rho * T
-        d7 = (s[6] / s[4] - 1) * rT * ux * (Kx * dux - Ky * duy) \
-            + (s[6] / s[5] - 1) * rT * uy * (Kx * duy + Ky * dux)
-        d8 = (s[7] / s[5] - 1) * rT * ux * (Kx * duy + Ky * dux) \
-            + (s[7] / s[4] - 1) * rT * uy * (Kx * dux - Ky * duy)
-        G -= p.dt * (np.outer(Minv[:, 6], d7) + np.outer(Minv[:, 7], d8))
-    return G
-
-
 @pytest.mark.parametrize("modified", [True, False])
 def test_linearised_step_is_papers_amplification_matrix(modified):
     nx, ny = 6, 5
@@ -233,7 +194,7 @@ def test_linearised_step_is_papers_amplification_matrix(modified):
         ky = 2 * np.pi * my / (ny * p.dy)
         ph = np.exp(1j * (kx * p.dx * np.arange(nx)[None, :] + ky * p.dy * np.arange(ny)[:, None]))
         Gnum = np.einsum("qpyx,yx->qp", J[:, 0, 0], ph)
-        Gp = _paper_G(p, rho, ux, uy, T, kx, ky)
+        Gp = amplification_matrix(p, rho, ux, uy, T, kx, ky)
         assert np.abs(Gnum - Gp).max() < 1e-11, (mx, my, np.abs(Gnum - Gp).max())
 
 
