@@ -46,9 +46,19 @@ __global__ void __launch_bounds__(BX, MINB) step_tiled_kernel(const __grid_const
   }
 }
 
-// FP32 with two nodes per thread (march_pair.cuh): BX columns, BX/2 threads.
+// FP32 with two nodes per thread (march_pair.cuh): BX columns, BX/2 threads,
+// 255 registers, four CTAs per SM.  (A cap of 200 registers fits without
+// spills and lets five CTAs share an SM, but measured 4% slower on GB300.)
+#ifndef MRTLB_PAIR_MAXNREG
+#define MRTLB_PAIR_MAXNREG 0
+#endif
 template <int BX, int NSLOT, int MINB>
-__global__ void __launch_bounds__(BX / 2, MINB)
+__global__ void
+#if MRTLB_PAIR_MAXNREG > 0
+    __maxnreg__(MRTLB_PAIR_MAXNREG)
+#else
+    __launch_bounds__(BX / 2, MINB)
+#endif
     step_pair_kernel(const __grid_constant__ CUtensorMap tmap, float* __restrict__ fout, const Layout L,
                      const __grid_constant__ Coef<P2> c, int* err, const int seglen) {
   using SM = PairSmem<BX, NSLOT>;
@@ -165,6 +175,14 @@ int plan_tiled(const Layout& L, int esize, void* f0, void* f1, TiledPlan* plan) 
   // resident CTAs per SM (shared memory and the launch bound); one full wave
   int per_sm = (int)((227 * 1024) / (plan->smem + 1024));
   if (per_sm > minb) per_sm = minb;
+  if (esize == 4 && MRTLB_PAIR) {  // the kernel launched for FP32: ask the runtime
+    constexpr int BX = Tile<float>::BX, NS = Tile<float>::NSLOT;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_pair_kernel<BX, NS, MRTLB_PAIR_MINB>, BX / 2,
+                                                      PairSmem<BX, NS>::bytes) == cudaSuccess && n > 0)
+      per_sm = n;
+    plan->smem = PairSmem<BX, NS>::bytes;
+  }
   if (per_sm < 1) per_sm = 1;
   plan_segments(L, nsm * per_sm, plan);
   plan->ok = true;
