@@ -143,18 +143,24 @@ struct PairMarch {
         if (act1) out[q * plane + 1] = vout[q].v.y;
       }
     }
-    const GhostTargets g0 = ghost_targets(L, x, j), g1 = ghost_targets(L, x + 1, j);
-    if (act0 && g0.any()) {
-      float v[16];
+#ifndef MRTLB_GHOST_GUARD
+#define MRTLB_GHOST_GUARD 1
+#endif
+    // only nodes on the grid's edges have ghosts to write
+    if (!MRTLB_GHOST_GUARD || j == 0 || j == L.ny - 1 || x == 0 || x + 1 >= L.nx - 1) {
+      const GhostTargets g0 = ghost_targets(L, x, j), g1 = ghost_targets(L, x + 1, j);
+      if (act0 && g0.any()) {
+        float v[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = vout[q].v.x;
-      write_ghosts(g0, plane, v, out);
-    }
-    if (act1 && g1.any()) {
-      float v[16];
+        for (int q = 0; q < 16; ++q) v[q] = vout[q].v.x;
+        write_ghosts(g0, plane, v, out);
+      }
+      if (act1 && g1.any()) {
+        float v[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = vout[q].v.y;
-      write_ghosts(g1, plane, v, out + 1);
+        for (int q = 0; q < 16; ++q) v[q] = vout[q].v.y;
+        write_ghosts(g1, plane, v, out + 1);
+      }
     }
     const bool bad0 = act0 && (!(mc.rho.v.x > 0.0f) || !(mc.T.v.x > 0.0f));
     const bool bad1 = act1 && (!(mc.rho.v.y > 0.0f) || !(mc.T.v.y > 0.0f));
