@@ -25,7 +25,9 @@
  *   (rho <= 0, T <= 0 or a non-finite value) met by a kernel is latched in a
  *   device error word and reported as MRTLB_ERR_NONPHYSICAL by the next
  *   synchronising call (mrtlb_macros, mrtlb_get_f, mrtlb_reduce,
- *   mrtlb_sync).
+ *   mrtlb_sync), as is an expired bounded wait (MRTLB_ERR_TIMEOUT).  The
+ *   word stays set until a new state is set (mrtlb_init_equilibrium,
+ *   mrtlb_set_f).
  * - Dense field layouts: a scalar field is [ny][nx] (x fastest); the
  *   distributions are [16][ny][nx], plane q = the paper's velocity i = q+1.
  */
@@ -156,6 +158,13 @@ int mrtlb_reduce(mrtlb_ctx* ctx, double out[5]);
  * staging buffer and one copy. */
 int mrtlb_get_f(mrtlb_ctx* ctx, void* f, int on_device);
 int mrtlb_set_f(mrtlb_ctx* ctx, const void* f, int on_device);
+
+/* Self-test of the device-side wait bound (the paper has no counterpart):
+ * one kernel waits on a barrier that nothing completes, gives up after the
+ * bound every kernel wait of the library uses (about 2 s) and flags it, so
+ * the call returns MRTLB_ERR_TIMEOUT; the error word is then cleared and the
+ * context stays usable.  Returns an earlier latched error instead, if any. */
+int mrtlb_selftest_wait(mrtlb_ctx* ctx);
 
 /* Wait for the context's stream; report any latched device error. */
 int mrtlb_sync(mrtlb_ctx* ctx);

@@ -437,6 +437,7 @@ extern "C" int mrtlb_init_equilibrium(mrtlb_ctx* c, const double* rho, const dou
     r = s; a = s + n; b = s + 2 * n; t = s + 3 * n;
   }
   c->cur = 0;
+  CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");  // a new run
   if (c->prec == MRTLB_FP64) launch_init_eq<double>(r, a, b, t, (double*)c->f[0], c->L, c->c64, c->stream);
   else launch_init_eq<float>(r, a, b, t, (float*)c->f[0], c->L, c->c64, c->stream);
   enqueue_bc(c, c->f[0]);
@@ -538,6 +539,19 @@ extern "C" int mrtlb_sync(mrtlb_ctx* c) {
   return sync_and_check(c);
 }
 
+extern "C" int mrtlb_selftest_wait(mrtlb_ctx* c) {
+  if (!bound(c)) return c ? fail(c, MRTLB_ERR_STATE, "bind state buffers first") : MRTLB_ERR_ARG;
+  int rc = sync_and_check(c);
+  if (rc) return rc;  // an error from earlier work comes first
+  launch_wait_selftest(c->err, c->stream);
+  rc = check_launch(c, "wait self-test");
+  if (rc) return rc;
+  rc = sync_and_check(c);
+  CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");
+  CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return rc;
+}
+
 extern "C" int mrtlb_macros(mrtlb_ctx* c, double* rho, double* ux, double* uy, double* T, int on_device) {
   if (!bound(c)) return c ? fail(c, MRTLB_ERR_STATE, "bind state buffers first") : MRTLB_ERR_ARG;
   const size_t n = (size_t)c->L.nx * c->L.ny;
@@ -621,6 +635,7 @@ extern "C" int mrtlb_set_f(mrtlb_ctx* c, const void* f, int on_device) {
     src = c->staging;
   }
   c->cur = 0;
+  CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");  // a new run
   if (c->prec == MRTLB_FP64) launch_pack<double>((const double*)src, (double*)c->f[0], c->L, c->stream);
   else launch_pack<float>((const float*)src, (float*)c->f[0], c->L, c->stream);
   enqueue_bc(c, c->f[0]);

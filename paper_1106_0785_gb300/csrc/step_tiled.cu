@@ -88,6 +88,19 @@ __global__ void
   }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that no
+// arrival completes; the wait gives up after its bound and the kernel flags
+// ERRBIT_TIMEOUT, as a stalled march would.  No copy is in flight.
+__global__ void wait_selftest_kernel(int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) atomicOr(err, ERRBIT_TIMEOUT);
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -249,6 +262,8 @@ void launch_step_tiled(const TiledPlan& plan, int cur, const Layout& L, const Co
                                                                  plan.seglen);
   }
 }
+
+void launch_wait_selftest(int* err, cudaStream_t st) { wait_selftest_kernel<<<1, 32, 0, st>>>(err); }
 
 template void launch_step_tiled<float>(const TiledPlan&, int, const Layout&, const Coef<float>&, int*,
                                        cudaStream_t, void*);

@@ -39,6 +39,9 @@ bool tiled_supported(const TiledPlan& plan);
 int encode_row_maps(const Layout& L, int esize, void* f0, void* f1, int bx, CUtensorMap out[2]);
 bool use_tiled(int which, const TiledPlan& plan, bool fp64);
 
+// One kernel whose bounded wait runs out (sets ERRBIT_TIMEOUT in *err).
+void launch_wait_selftest(int* err, cudaStream_t st);
+
 // Launch one step reading buffer `cur` and writing the other one.
 template <typename R>
 void launch_step_tiled(const TiledPlan& plan, int cur, const Layout& L, const Coef<R>& c, int* err,

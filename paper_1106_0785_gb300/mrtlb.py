@@ -48,7 +48,7 @@ EXPORTS = (
     "mrtlb_batch_create", "mrtlb_batch_step", "mrtlb_batch_sync", "mrtlb_batch_set_tiles",
     "mrtlb_batch_get_tiles", "mrtlb_batch_set_graph_steps", "mrtlb_batch_tune", "mrtlb_batch_nodes",
     "mrtlb_batch_last_error", "mrtlb_batch_destroy",
-    "mrtlb_set_rates", "mrtlb_get_rates", "mrtlb_adjoint_forward", "mrtlb_adjoint_set_interval", "mrtlb_adjoint_backward",
+    "mrtlb_set_rates", "mrtlb_get_rates", "mrtlb_selftest_wait", "mrtlb_adjoint_forward", "mrtlb_adjoint_set_interval", "mrtlb_adjoint_backward",
     "mrtlb_adjoint_release", "mrtlb_equilibrium_adjoint",
 )
 
@@ -136,6 +136,7 @@ def load(path=LIB_PATH):
     lib.mrtlb_set_rates.argtypes = [P, D]
     lib.mrtlb_get_rates.argtypes = [P, D]
     lib.mrtlb_adjoint_forward.argtypes = [P, ctypes.c_long]
+    lib.mrtlb_selftest_wait.argtypes = [P]
     lib.mrtlb_adjoint_set_interval.argtypes = [P, ctypes.c_long]
     lib.mrtlb_adjoint_backward.argtypes = [P, P, P, D, P]
     lib.mrtlb_adjoint_release.argtypes = [P]
@@ -210,6 +211,11 @@ def mrtlb_set_f(ctx, f, on_device):
 
 def mrtlb_sync(ctx):
     _check(load().mrtlb_sync(ctx), ctx)
+
+
+def mrtlb_selftest_wait(ctx):
+    """Returns the status code (MRTLB_ERR_TIMEOUT when the wait bound works)."""
+    return load().mrtlb_selftest_wait(ctx)
 
 
 def mrtlb_set_kernel(ctx, which):

@@ -342,3 +342,25 @@ def test_fp32_uniform_state_does_not_drift(cuda, kernel):
         r, a, b, t = sim.macros()
     assert np.abs(r / r0 - 1).max() < 1e-6 and np.abs(t / t0 - 1).max() < 1e-6
     assert np.abs(a - a0).max() < 1e-6 and np.abs(b - b0).max() < 1e-6
+
+
+def test_bounded_wait_reports_a_timeout_and_the_context_recovers(cuda):
+    """A kernel wait that cannot complete gives up after its bound (about
+    2 s): the host reads MRTLB_ERR_TIMEOUT, the error word is cleared, and
+    the context keeps stepping correctly."""
+    import time
+    cfg = _cfg(64, 8, BCS["periodic"], "fp64")
+    (rho, ux, uy, T), nz = _input(cfg, 97)
+    p = oracle_params(cfg)
+    f0 = fdlb.prepare(oeq.feq(rho, ux, uy, T) + nz, p)
+    with Simulation(cfg) as sim:
+        sim.set_f(f0)
+        t0 = time.perf_counter()
+        rc = M.mrtlb_selftest_wait(sim.ctx)
+        waited = time.perf_counter() - t0
+        assert rc == M.MRTLB_ERR_TIMEOUT
+        assert 1.5 < waited < 30.0
+        sim.step(3)
+        sim.sync()
+        g = sim.get_f()
+    assert rel_plane_err(g, fdlb.run(f0, p, 3)) < 1e-12
