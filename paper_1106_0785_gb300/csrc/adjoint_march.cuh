@@ -227,8 +227,9 @@ struct AdjMarch {
 
 // One CTA per (strip, row segment): strips x0 = blockIdx.x * SX, output
 // rows -1 + blockIdx.y * seglen ... (clipped at ny + 1).
+// (FP32: three CTAs per SM, the shared-memory limit, so at most 170 registers)
 template <typename R, int BX, int NF, int NL>
-__global__ void __launch_bounds__(BX, 1)
+__global__ void __launch_bounds__(BX, sizeof(R) == 4 ? 3 : 1)
     adj_march_kernel(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap lmap,
                      R* __restrict__ out, const Layout L, const __grid_constant__ AdjCoef<R> a, double* gacc,
                      int* err,
