@@ -22,6 +22,11 @@ def _instances(precision):
     for nx, ny, Pr, U in ((130, 12, 0.5, 0.4), (257, 7, 2.0, 0.8), (64, 33, 1.3, 0.2)):
         out.append(workloads.couette(Pr=Pr, nx=nx, ny=ny, precision=precision, U=U))
     out.append(workloads.richtmyer_meshkov(nx=200, ny=36, precision=precision))
+    # the boundary kinds of Sec. IV B and IV A: inflow, outflow and reflecting
+    # sides (a small shock-bubble grid) and diffuse-reflection walls
+    cfg, fields = workloads.shock_bubble(nx=600, ny=30, precision=precision, radius=10.0)
+    out.append((cfg, fields))
+    out.append(workloads.slip_couette(nx=100, ny=5, precision=precision))
     return out
 
 
