@@ -492,6 +492,9 @@ def run_batched(args, world, dev):
 def main():
     args = parse()
     if args.impl == "reference":
+        # one thread, as the line reports (before anything loads numpy's BLAS)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
         world, rank, _ = dist_init("gloo")
         run_reference(args, world, rank)
         return
