@@ -2,7 +2,8 @@
 
 Forward: the initial state is the equilibrium of (rho0, ux0, uy0, T0)
 (device FP64 [ny][nx] tensors), the rates s (16) are set on the context,
-K steps run with sqrt(K) checkpoints (mrtlb_adjoint_forward), and the final
+K steps run keeping what the backward pass needs (mrtlb_adjoint_forward:
+every state when they fit, else sqrt(K) checkpoints), and the final
 macroscopic fields come back as device FP64 tensors.  Backward: the
 hand-written adjoint kernels (mrtlb_adjoint_backward) give dL/ds and
 dL/df0, and mrtlb_equilibrium_adjoint maps dL/df0 to the initial fields, so

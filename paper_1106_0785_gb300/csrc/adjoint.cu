@@ -17,10 +17,12 @@
 // neighbour (walls themselves get zero).  Gradients with respect to the
 // rates s_5..s_16 accumulate in FP64.
 //
-// K steps use sqrt(K) checkpointing: adjoint_forward stores the state every
-// S = ceil(sqrt(K)) steps; backward recomputes each segment's S states on
-// separate work buffers (the context keeps f^K) and runs the adjoint steps
-// through it in reverse.
+// K steps run in segments of S: adjoint_forward keeps the states of the
+// last segment in slots (all K states, S = K, when K + 2 states fit in half
+// the free memory; else S = ceil(sqrt(K)) with a checkpoint per segment);
+// backward recomputes any segment whose states are not held from its
+// checkpoint (the context keeps f^K) and runs the adjoint steps through it
+// in reverse.  A later forward pass of the same shape reuses the buffers.
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -243,7 +243,8 @@ void launch_init_eq(const double* rho, const double* ux, const double* uy, const
 // rho, u, T in FP64 (Sec. II, R = 1).
 // ---------------------------------------------------------------------------
 // Moment sums in the storage precision (FP32 states: the same recovery as
-// the step, FP32 sums and an FP64 temperature numerator), outputs in FP64.
+// the step, FP32 sums and the compensated temperature numerator), outputs
+// in FP64.
 template <typename R>
 __global__ void macros_kernel(const R* __restrict__ f, double* rho_o, double* ux_o, double* uy_o,
                               double* T_o, Layout L) {

@@ -124,8 +124,9 @@ MRTLB_HD void conserved(const R f[16], R& rho, R& jx, R& jy, R& e) {
 
 // Temperature from the conserved moments (Sec. II with R = 1):
 // T = (e rho - |j|^2 / 2) / rho^2.  The numerator, where the kinetic part
-// cancels against e behind strong shocks, is formed in FP64 from the exact
-// FP64 products of the FP32 moments; only the final scaling is FP32.
+// cancels against e behind strong shocks, is formed to about twice FP32
+// precision (below; MRTLB_TEMP_COMPENSATED = 0 forms it in FP64 from the
+// exact FP64 products of the FP32 moments); the final scaling is FP32.
 #ifndef MRTLB_TEMP_COMPENSATED
 #define MRTLB_TEMP_COMPENSATED 1
 #endif
