@@ -255,9 +255,16 @@ int bfail(mrtlb_batch* b, int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return bfail(b, MRTLB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e_)); \
   } while (0)
 
+#ifndef MRTLB_BATCH_MINB64
+#define MRTLB_BATCH_MINB64 8
+#endif
+#ifndef MRTLB_BATCH_MINB128
+#define MRTLB_BATCH_MINB128 4
+#endif
+
 int resident_per_sm(int prec, int bx) {
   if (prec == MRTLB_FP64) return 3;
-  return bx == 64 ? 8 : 4;
+  return bx == 64 ? MRTLB_BATCH_MINB64 : MRTLB_BATCH_MINB128;
 }
 
 bool shape_supported(int prec, int bx) {
@@ -345,9 +352,9 @@ void enqueue_batch_step(mrtlb_batch* b, int cur, cudaStream_t st) {
   if (b->prec == MRTLB_FP64) {
     launch_batched_bx<double, 64, 3>(b->d_insts, b->d_tiles, b->ntiles, b->grid, cur, b->err, st);
   } else if (b->bx == 64) {
-    launch_batched_bx<float, 64, 8>(b->d_insts, b->d_tiles, b->ntiles, b->grid, cur, b->err, st);
+    launch_batched_bx<float, 64, MRTLB_BATCH_MINB64>(b->d_insts, b->d_tiles, b->ntiles, b->grid, cur, b->err, st);
   } else {
-    launch_batched_bx<float, 128, 4>(b->d_insts, b->d_tiles, b->ntiles, b->grid, cur, b->err, st);
+    launch_batched_bx<float, 128, MRTLB_BATCH_MINB128>(b->d_insts, b->d_tiles, b->ntiles, b->grid, cur, b->err, st);
   }
 }
 

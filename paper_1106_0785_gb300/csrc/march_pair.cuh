@@ -9,6 +9,13 @@
 // Of the x-neighbours of the pair, the inner ones are the pair's own values
 // and the outer ones one 4-byte load each.  u of the two strip halo
 // columns comes from lanes 0 and 1.  A CTA has BX/2 threads.
+//
+// Only row j-1 of the pair's columns stays in registers from one row to
+// the next: rows j and j+1 are read from their ring slots, and u, 1/rho
+// and T of each row go to a 4-row shared ring when the row arrives.  (The
+// earlier form kept rows j-1, j, j+1 and their macros in registers and
+// shifted them down after every row: 254 registers against 211 now, and
+// about 2% slower on GB300.)
 #pragma once
 
 #include <cuda.h>
@@ -23,7 +30,7 @@ struct PairSmem {
   using S = Smem<float, BX, NSLOT>;  // the same TMA slots as the scalar march
   static constexpr int HL = S::HL, BW = S::BW, SLOT = S::SLOT;
   static constexpr int UW = BX + 4;          // u row: halo x0-1 at 1, column c at 2 + c, x0+BX at BX+2
-  static constexpr int UROW = 2 * UW;        // u_x row then u_y row
+  static constexpr int UROW = 4 * UW;        // per ring row: u_x, u_y, 1/rho, T
   static constexpr size_t slot_bytes = S::slot_bytes;
   static constexpr size_t u_off = (size_t)NSLOT * slot_bytes;
   static constexpr size_t bar_off = (u_off + (size_t)4 * UROW * sizeof(float) + 15) & ~(size_t)15;
@@ -85,54 +92,87 @@ struct PairMarch {
     n_last = jb;
     n_issued = 0;
   }
-  // the pair's own columns of row r, their macros, and u published to the ring
-  __device__ __forceinline__ void arrive(int r, P2 f[16], NodeMac<P2>& m) const {
+  // The pair's own columns of row r into f, and their u, 1/rho and T
+  // published to the ring (u also of the strip's two halo columns).
+  __device__ __forceinline__ void arrive(int r, P2 f[16]) const {
     const float* sl = slot(r);
 #pragma unroll
     for (int q = 0; q < 16; ++q) f[q] = P2(*reinterpret_cast<const float2*>(sl + q * SM::BW + SM::HL + 2 * t));
-    m = node_macros(f);
-    float* u = urow(r);
-    *reinterpret_cast<float2*>(u + 2 + 2 * t) = m.ux.v;
-    *reinterpret_cast<float2*>(u + SM::UW + 2 + 2 * t) = m.uy.v;
+    const NodeMac<P2> m = node_macros(f);
+    float* u = urow(r) + 2 + 2 * t;
+    *reinterpret_cast<float2*>(u) = m.ux.v;
+    *reinterpret_cast<float2*>(u + SM::UW) = m.uy.v;
+    *reinterpret_cast<float2*>(u + 2 * SM::UW) = m.ir.v;
+    *reinterpret_cast<float2*>(u + 3 * SM::UW) = m.T.v;
     if (t < 2) {  // halo columns x0-1 (t = 0) and x0+BX (t = 1)
       const int col = (t == 0) ? SM::HL - 1 : SM::HL + BX;
       float g[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) g[q] = sl[q * SM::BW + col];
       const NodeMac<float> mh = node_macros(g);
-      const int ui = (t == 0) ? 1 : BX + 2;
-      u[ui] = mh.ux;
-      u[SM::UW + ui] = mh.uy;
+      float* uh = urow(r) + ((t == 0) ? 1 : BX + 2);
+      uh[0] = mh.ux;
+      uh[SM::UW] = mh.uy;
     }
   }
-  // one output row j for both columns; fp/fc hold rows j-1, j, fn receives
-  // row j+1.  Returns true if the CTA must stop (a wait expired).
-  __device__ __forceinline__ bool row(int j, const Coef<P2>& c, const P2 (&fp)[16], const P2 (&fc)[16],
-                                      P2 (&fn)[16], const NodeMac<P2>& mp, const NodeMac<P2>& mc,
-                                      NodeMac<P2>& mn) {
-    const bool bad = !ready(j + 1);
-    arrive(j + 1, fn, mn);
-    if (__syncthreads_or(bad)) return true;
+  __device__ __forceinline__ static P2 ld2(const float* p) { return P2(*reinterpret_cast<const float2*>(p)); }
+
+  // One output row j for both columns.  Row j-1 of the pair's columns is
+  // in fp; row j is read from its slot into fc (the caller's fp of the next
+  // row), row j+1 from its slot; rho, j and e are recomputed from the
+  // harmonics the collision needs anyway, u, 1/rho and T come from the
+  // ring.  Returns true if the CTA must stop (a wait expired).
+  __device__ __forceinline__ bool row(int j, const Coef<P2>& c, const P2 (&fp)[16], P2 (&fc)[16]) {
+    if (__syncthreads_or(!ready(j + 1))) return true;
     if (t == 0) refill();
+    // row j+1's u, 1/rho and T go to the ring in the same block as row j's
+    // update (other threads read them only after the next barrier), so that
+    // the two interleave
+    {
+      P2 fn[16];
+      arrive(j + 1, fn);
+    }
     const float* sc = slot(j);
+    const float* sn = slot(j + 1);
+    const int o = SM::HL + 2 * t;  // slot column of x
+#pragma unroll
+    for (int q = 0; q < 16; ++q) fc[q] = ld2(sc + q * SM::BW + o);
+    Harm<P2> h;
+    harmonics(fc, h);
+    P2 rho, jx, jy, e;
+    conserved_h(h, rho, jx, jy, e);
     const float* u = urow(j);
+    const float* un = urow(j + 1);
+    const float* up = urow(j - 1);
     const int ui = 2 + 2 * t;  // ring index of column x
+    const P2 ux = ld2(u + ui), uy = ld2(u + SM::UW + ui);
+    const P2 ir = ld2(u + 2 * SM::UW + ui), T = ld2(u + 3 * SM::UW + ui);
     const P2 uxE(u[ui + 1], u[ui + 2]), uxW(u[ui - 1], u[ui]);
     const P2 uyE(u[SM::UW + ui + 1], u[SM::UW + ui + 2]), uyW(u[SM::UW + ui - 1], u[SM::UW + ui]);
     const P2 dux_dx = P2((uxE - uxW) * c.inv2dx), duy_dx = P2((uyE - uyW) * c.inv2dx);
-    const P2 dux_dy = P2((mn.ux - mp.ux) * c.inv2dy), duy_dy = P2((mn.uy - mp.uy) * c.inv2dy);
+    const P2 dux_dy = P2((ld2(un + ui) - ld2(up + ui)) * c.inv2dy);
+    const P2 duy_dy = P2((ld2(un + SM::UW + ui) - ld2(up + SM::UW + ui)) * c.inv2dy);
     P2 C[16];
-    collision(c, fc, dux_dx, dux_dy, duy_dx, duy_dy, mc.rho, mc.ir, mc.jx, mc.jy, mc.e, mc.ux, mc.uy,
-              mc.T, C);
+    collision_h(c, h, dux_dx, dux_dy, duy_dx, duy_dy, rho, ir, jx, jy, e, ux, uy, T, C);
     float* out = fout + L.node(x, j);
     P2 vout[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int b = q * SM::BW + SM::HL + 2 * t;
+      const int b = q * SM::BW + o;
       const P2 fE = (vx_of(q) != 0) ? P2(fc[q].v.y, sc[b + 2]) : P2(0.0f);
       const P2 fW = (vx_of(q) != 0) ? P2(sc[b - 1], fc[q].v.x) : P2(0.0f);
-      vout[q] = lw_update(c, q, fc[q], C[q], fE, fW, fn[q], fp[q]);
+      const P2 fN = (vy_of(q) != 0) ? ld2(sn + b) : P2(0.0f);
+      vout[q] = lw_update(c, q, fc[q], C[q], fE, fW, fN, fp[q]);
     }
+    store_row(j, out, vout);
+    const bool bad0 = act0 && (!(rho.v.x > 0.0f) || !(T.v.x > 0.0f));
+    const bool bad1 = act1 && (!(rho.v.y > 0.0f) || !(T.v.y > 0.0f));
+    if (bad0 || bad1) atomicOr(err, ERRBIT_NONPHYSICAL);
+    return false;
+  }
+
+  // the row's new values to the output buffer, and to the ghosts they feed
+  __device__ __forceinline__ void store_row(int j, float* out, const P2 (&vout)[16]) const {
     if (act0 && act1) {
 #pragma unroll
       for (int q = 0; q < 16; ++q) *reinterpret_cast<float2*>(out + q * plane) = vout[q].v;
@@ -162,10 +202,6 @@ struct PairMarch {
         write_ghosts(g1, plane, v, out + 1);
       }
     }
-    const bool bad0 = act0 && (!(mc.rho.v.x > 0.0f) || !(mc.T.v.x > 0.0f));
-    const bool bad1 = act1 && (!(mc.rho.v.y > 0.0f) || !(mc.T.v.y > 0.0f));
-    if (bad0 || bad1) atomicOr(err, ERRBIT_NONPHYSICAL);
-    return false;
   }
 
   // Advance rows [ja, jb) of the strip at x0 (a multiple of BX); as March.
@@ -184,22 +220,16 @@ struct PairMarch {
     }
     issued_to = min(r_first + max(pre, NSLOT) - 1, r_last);
 
-    P2 F0[16], F1[16], F2[16];
-    NodeMac<P2> M0, M1, M2;
+    P2 FA[16], FB[16];  // rows j-1 (FA) and j (FB) of the pair's columns
     bool bad = !ready(r_first);
-    arrive(r_first, F0, M0);
+    arrive(r_first, FA);
     bad |= !ready(ja);
-    arrive(ja, F1, M1);
+    arrive(ja, FB);  // (u, 1/rho, T of row ja; its f is read again from the slot)
     bool stopped = __syncthreads_or(bad);
     for (int j = ja; !stopped && j < jb; ++j) {
-      if ((stopped = row(j, c, F0, F1, F2, M0, M1, M2))) break;
+      if ((stopped = row(j, c, FA, FB))) break;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        F0[q] = F1[q];
-        F1[q] = F2[q];
-      }
-      M0 = M1;
-      M1 = M2;
+      for (int q = 0; q < 16; ++q) FA[q] = FB[q];
     }
     if (!stopped) kbase += r_last - r_first + 1;
     return stopped;

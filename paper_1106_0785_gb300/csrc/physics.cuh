@@ -111,15 +111,20 @@ MRTLB_HD void moments(const Harm<R>& h, R m[16]) {
   m[13] = R(2) * h.P[0] + R(32) * h.P[1];
 }
 
-// Conserved moments only: rho, j_x, j_y, e (rows 1-4 of M).
+// Conserved moments only: rho, j_x, j_y, e (rows 1-4 of M), from the
+// harmonics or from f.
 template <typename R>
-MRTLB_HD void conserved(const R f[16], R& rho, R& jx, R& jy, R& e) {
-  Harm<R> h;
-  harmonics(f, h);
+MRTLB_HD void conserved_h(const Harm<R>& h, R& rho, R& jx, R& jy, R& e) {
   rho = (h.S[0] + h.S[1]) + (h.S[2] + h.S[3]);
   e = R(0.5) * h.S[0] + h.S[1] + R(2) * h.S[2] + R(4) * h.S[3];
   jx = (h.X[0] + h.X[1]) + R(2) * (h.X[2] + h.X[3]);
   jy = (h.Y[0] + h.Y[1]) + R(2) * (h.Y[2] + h.Y[3]);
+}
+template <typename R>
+MRTLB_HD void conserved(const R f[16], R& rho, R& jx, R& jy, R& e) {
+  Harm<R> h;
+  harmonics(f, h);
+  conserved_h(h, rho, jx, jy, e);
 }
 
 // Temperature from the conserved moments (Sec. II with R = 1):
@@ -342,14 +347,13 @@ MRTLB_HD void inverse_nonconserved(const Coef<R>& c, const R m[16], R f[16]) {
 
 // dt * C = dt * M^-1 c with c_k = s_k (f^_k - f^eq_k) for k >= 4 (the
 // conserved components vanish) and the modification of Sec. II added to
-// k = 6, 7 (the paper's 7 and 8).  grad = (dux/dx, dux/dy, duy/dx, duy/dy).
-// Also returns rho and T through the out-parameters for error checks.
+// k = 6, 7 (the paper's 7 and 8), from the node's moments, macroscopic
+// state and velocity gradients (dux/dx, dux/dy, duy/dx, duy/dy).
+// collision_h takes the harmonics of f, collision f itself.
 template <typename R>
-__device__ __forceinline__ void collision(const Coef<R>& c, const R f[16], R dux_dx, R dux_dy,
-                                          R duy_dx, R duy_dy, R rho, R inv_rho, R jx, R jy, R e,
-                                          R ux, R uy, R T, R C[16]) {
-  Harm<R> h;
-  harmonics(f, h);
+__device__ __forceinline__ void collision_h(const Coef<R>& c, const Harm<R>& h, R dux_dx, R dux_dy,
+                                            R duy_dx, R duy_dy, R rho, R inv_rho, R jx, R jy, R e,
+                                            R ux, R uy, R T, R C[16]) {
   R m[16];
   moments(h, m);
   R eq[16];
@@ -367,6 +371,14 @@ __device__ __forceinline__ void collision(const Coef<R>& c, const R f[16], R dux
   }
   cc[0] = cc[1] = cc[2] = cc[3] = R(0);
   inverse_nonconserved(c, cc, C);
+}
+template <typename R>
+__device__ __forceinline__ void collision(const Coef<R>& c, const R f[16], R dux_dx, R dux_dy,
+                                          R duy_dx, R duy_dy, R rho, R inv_rho, R jx, R jy, R e,
+                                          R ux, R uy, R T, R C[16]) {
+  Harm<R> h;
+  harmonics(f, h);
+  collision_h(c, h, dux_dx, dux_dy, duy_dx, duy_dy, rho, inv_rho, jx, jy, e, ux, uy, T, C);
 }
 
 }  // namespace mrtlb

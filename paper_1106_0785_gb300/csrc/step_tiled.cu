@@ -47,8 +47,10 @@ __global__ void __launch_bounds__(BX, MINB) step_tiled_kernel(const __grid_const
 }
 
 // FP32 with two nodes per thread (march_pair.cuh): BX columns, BX/2 threads,
-// 255 registers, four CTAs per SM.  (A cap of 200 registers fits without
-// spills and lets five CTAs share an SM, but measured 4% slower on GB300.)
+// 211 registers, four CTAs per SM.  Measured alternatives on GB300: a launch
+// bound of five CTAs (168 registers: three warps share an SM sub-partition's
+// register file) was 7% slower, 64-column strips with eight one-warp CTAs
+// 5% slower.
 #ifndef MRTLB_PAIR_MAXNREG
 #define MRTLB_PAIR_MAXNREG 0
 #endif
@@ -123,7 +125,10 @@ EncodeFn get_encode() {
 // tile shapes: FP32 128-node strips, 4-slot ring, 4 CTAs per SM;
 // FP64 64-node strips (same box bytes), 4-slot ring
 template <typename R> struct Tile;
-template <> struct Tile<float> { static constexpr int BX = 128, NSLOT = 4, MINB = 4; };
+#ifndef MRTLB_PAIR_BX
+#define MRTLB_PAIR_BX 128
+#endif
+template <> struct Tile<float> { static constexpr int BX = MRTLB_PAIR_BX, NSLOT = 4, MINB = 4; };
 template <> struct Tile<double> { static constexpr int BX = 64, NSLOT = 4, MINB = 1; };
 
 #ifndef MRTLB_PAIR
