@@ -18,6 +18,8 @@ Printed JSON line (rank 0):
              16 writes) / its mean launch time, against measured HBM copy
              bandwidth
   fp64_mlups the all-FP64 path on the same input
+  compute    the step's flop rate (counted flops per node update) against
+             fused multiply-add ceilings measured on the device
   cpu_baseline  the FP64 numpy oracle on a crop of the same input, one thread
 
 Multi-GPU (torchrun): every rank advances its own replica (weak scaling, no
@@ -39,6 +41,11 @@ sys.path.insert(0, ROOT)
 
 NX, NY = 4096, 1024
 BYTES_PER_LUP_FP32 = 128
+# Floating-point operations of one node update (a fused multiply-add counts
+# two), counted by running the step kernels' own per-node templates with an
+# operation-counting number type (tests/flopcount/step_flops.cu; the CPU
+# test suite keeps these equal to its output).
+STEP_FLOPS_PER_LUP = {"fp32": 539, "fp64": 521}
 CROP = (1600, 0, 512, 128)      # x0, y0, nx, ny of the CPU-baseline crop
 REF_CROP = (1900, 0, 128, 64)   # per-step sample of the reference arm
 
@@ -330,6 +337,16 @@ def run_mine(args, world, rank, local):
                 "kernel": "step_pair_kernel<128,4,4>", "kernel_ms_mean": kavg_s * 1e3,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, copy)"}
 
+    # ---- compute side: measured FMA ceilings, outside the timed region -----
+    ceil = {k: M.mrtlb_measure_peak(v) for k, v in (("fp32", M.MRTLB_PEAK_FP32),
+                                                    ("fp32_pair", M.MRTLB_PEAK_FP32_PAIR),
+                                                    ("fp64", M.MRTLB_PEAK_FP64))}
+    step_tflops = STEP_FLOPS_PER_LUP["fp32"] * nodes / kavg_s / 1e12
+    compute = {"unit": "TFLOP/s", "flops_per_lup": STEP_FLOPS_PER_LUP,
+               "step_fp32": step_tflops, "ceiling_fp32": ceil["fp32"],
+               "ceiling_fp32_pair": ceil["fp32_pair"], "ceiling_fp64": ceil["fp64"],
+               "step_frac_of_fp32": step_tflops / ceil["fp32"] if ceil["fp32"] > 0 else None}
+
     # ---- e2e through the C ABI with host buffers ---------------------------
     f_host = torch.empty((16, NY, NX), dtype=torch.float32, pin_memory=True)
     sim.get_f()  # warm the staging buffer
@@ -375,6 +392,8 @@ def run_mine(args, world, rank, local):
     sim64.sync()
     sim64.close()
     fp64_mlups = world * nodes * args.fp64_steps / (ms64 / 1e3) / 1e6
+    compute["step_fp64"] = STEP_FLOPS_PER_LUP["fp64"] * fp64_mlups / world / 1e6
+    compute["step_frac_of_fp64"] = compute["step_fp64"] / ceil["fp64"] if ceil["fp64"] > 0 else None
 
     # ---- the batched set: 64 uneven Sod-type / Couette instances -----------
     batched = None
@@ -395,6 +414,7 @@ def run_mine(args, world, rank, local):
         "e2e": e2e,
         "gpu_launches": launches,
         "roofline": roofline,
+        "compute": compute,
         "fp64_mlups": fp64_mlups,
         "fp64_ms_per_step": ms64 / args.fp64_steps,
         "batched": batched,

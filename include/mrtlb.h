@@ -189,6 +189,20 @@ int mrtlb_set_kernel(mrtlb_ctx* ctx, int which);
 int mrtlb_timing_begin(mrtlb_ctx* ctx, int max_launches);
 int mrtlb_timing_end(mrtlb_ctx* ctx, double* kernel_ms, long* launches);
 
+/* Measured arithmetic ceiling of the current device, for the roofline of
+ * the step beside the HBM bound (the paper has no counterpart).  One kernel
+ * runs independent fused multiply-add chains on every SM at full occupancy,
+ * with no memory traffic; the best of three timed launches (after one warm-up,
+ * on a private stream, CUDA events) is returned in TFLOP/s, a fused
+ * multiply-add counting two.  kind: MRTLB_PEAK_FP32 (scalar FP32),
+ * MRTLB_PEAK_FP32_PAIR (packed FP32 pairs, the form the FP32 step uses),
+ * MRTLB_PEAK_FP64.  Synchronous; about 0.1 s.  MRTLB_ERR_ARG for another kind
+ * or a NULL output, MRTLB_ERR_CUDA if a launch fails. */
+#define MRTLB_PEAK_FP32 0
+#define MRTLB_PEAK_FP32_PAIR 1
+#define MRTLB_PEAK_FP64 2
+int mrtlb_measure_peak(int kind, double* tflops);
+
 /* Kernel launches one time step enqueues (boundary fills and the step). */
 int mrtlb_launches_per_step(const mrtlb_ctx* ctx);
 

@@ -87,22 +87,6 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <typename R>
-struct NodeMac {
-  R rho, ir, jx, jy, e, ux, uy, T;
-};
-
-template <typename R>
-__device__ __forceinline__ NodeMac<R> node_macros(const R g[16]) {
-  NodeMac<R> m;
-  conserved(g, m.rho, m.jx, m.jy, m.e);
-  m.ir = recip(m.rho);
-  m.ux = m.jx * m.ir;
-  m.uy = m.jy * m.ir;
-  m.T = temperature(m.rho, m.jx, m.jy, m.e, m.ir);
-  return m;
-}
-
 template <typename R, int BX, int NSLOT>
 struct Smem {
   static_assert((NSLOT & (NSLOT - 1)) == 0 && NSLOT >= 4, "NSLOT: power of two >= 4");

@@ -130,35 +130,47 @@ MRTLB_HD void conserved(const R f[16], R& rho, R& jx, R& jy, R& e) {
 // Temperature from the conserved moments (Sec. II with R = 1):
 // T = (e rho - |j|^2 / 2) / rho^2.  The numerator, where the kinetic part
 // cancels against e behind strong shocks, is formed to about twice FP32
-// precision (below; MRTLB_TEMP_COMPENSATED = 0 forms it in FP64 from the
-// exact FP64 products of the FP32 moments); the final scaling is FP32.
+// precision (temperature_compensated; MRTLB_TEMP_COMPENSATED = 0 forms it in
+// FP64 from the exact FP64 products of the FP32 moments); the final scaling
+// is FP32.
+//
+// temperature_compensated: N = e rho - (jx^2 + jy^2)/2 to about twice the
+// working precision, each product split exactly into its rounded value and
+// error (Dekker's TwoProduct in its fused multiply-add form), the two large
+// cancellations done with Dekker's Fast2Sum, which is exact when the first
+// operand is the larger; here e rho >= (jx^2 + jy^2)/2 whenever T >= 0.
+static_assert(sizeof(decltype(fma(1.0f, 1.0f, 1.0f))) == sizeof(float), "fma on floats must stay in FP32");
+template <typename R>
+MRTLB_HD R temperature_compensated(R rho, R jx, R jy, R e, R inv_rho) {
+  const R p = e * rho, ep = fma(e, rho, -p);
+  const R hx = R(0.5f) * jx, hy = R(0.5f) * jy;  // exact
+  const R a = hx * jx, ea = fma(hx, jx, -a);
+  const R b = hy * jy, eb = fma(hy, jy, -b);
+  const R s1 = p - a, t1 = (p - s1) - a;
+  const R s2 = s1 - b, t2 = (s1 - s2) - b;
+  const R num = s2 + ((t1 + t2) + ((ep - ea) - eb));
+  return R(num * R(inv_rho * inv_rho));
+}
 #ifndef MRTLB_TEMP_COMPENSATED
 #define MRTLB_TEMP_COMPENSATED 1
 #endif
 __device__ __forceinline__ float temperature(float rho, float jx, float jy, float e, float inv_rho) {
 #if MRTLB_TEMP_COMPENSATED
-  // N = e rho - (jx^2 + jy^2)/2 in FP32 arithmetic to about twice FP32
-  // precision: each product split exactly into its rounded value and error
-  // (Dekker's TwoProduct in its fused multiply-add form), the two large
-  // cancellations done with Dekker's Fast2Sum, which is exact when the first
-  // operand is the larger; here e rho >= (jx^2 + jy^2)/2 whenever T >= 0.
-  const float p = e * rho, ep = fmaf(e, rho, -p);
-  const float hx = 0.5f * jx, hy = 0.5f * jy;  // exact
-  const float a = hx * jx, ea = fmaf(hx, jx, -a);
-  const float b = hy * jy, eb = fmaf(hy, jy, -b);
-  const float s1 = p - a, t1 = (p - s1) - a;
-  const float s2 = s1 - b, t2 = (s1 - s2) - b;
-  const float num = s2 + ((t1 + t2) + ((ep - ea) - eb));
-  return num * (inv_rho * inv_rho);
+  return temperature_compensated(rho, jx, jy, e, inv_rho);
 #else
   const double j2 = fma((double)jy, (double)jy, (double)jx * (double)jx);
   const double num = fma((double)e, (double)rho, -0.5 * j2);
   return (float)num * (inv_rho * inv_rho);
 #endif
 }
+// (FP64 states: the plain formula)
+template <typename R>
+MRTLB_HD R temperature_plain(R rho, R jx, R jy, R e, R inv_rho) {
+  const R j2 = fma(jy, jy, R(jx * jx));
+  return R(fma(e, rho, R(R(-0.5) * j2)) * R(inv_rho * inv_rho));
+}
 __device__ __forceinline__ double temperature(double rho, double jx, double jy, double e, double inv_rho) {
-  const double j2 = fma(jy, jy, jx * jx);
-  return fma(e, rho, -0.5 * j2) * (inv_rho * inv_rho);
+  return temperature_plain(rho, jx, jy, e, inv_rho);
 }
 
 // 1/x: the hardware approximation refined by one Newton-Raphson step
@@ -181,16 +193,25 @@ __device__ __forceinline__ P2 recip(P2 x) {
   return P2(r * fma(-x, r, P2(2.0f)));
 }
 __device__ __forceinline__ P2 temperature(P2 rho, P2 jx, P2 jy, P2 e, P2 inv_rho) {
-  const P2 p = e * rho, ep = fma(e, rho, -p);
-  const P2 hx = P2(0.5f) * jx, hy = P2(0.5f) * jy;
-  const P2 a = hx * jx, ea = fma(hx, jx, -a);
-  const P2 b = hy * jy, eb = fma(hy, jy, -b);
-  const P2 s1 = p - a, t1 = (p - s1) - a;
-  const P2 s2 = s1 - b, t2 = (s1 - s2) - b;
-  const P2 num = s2 + ((t1 + t2) + ((ep - ea) - eb));
-  return P2(num * P2(inv_rho * inv_rho));
+  return temperature_compensated(rho, jx, jy, e, inv_rho);
 }
 __device__ __forceinline__ P2 expr(P2 x) { return P2(expf(x.v.x), expf(x.v.y)); }
+
+// The macroscopic state of one node: the conserved moments, 1/rho, u and T.
+template <typename R>
+struct NodeMac {
+  R rho, ir, jx, jy, e, ux, uy, T;
+};
+template <typename R>
+MRTLB_HD NodeMac<R> node_macros(const R g[16]) {
+  NodeMac<R> m;
+  conserved(g, m.rho, m.jx, m.jy, m.e);
+  m.ir = recip(m.rho);
+  m.ux = R(m.jx * m.ir);
+  m.uy = R(m.jy * m.ir);
+  m.T = temperature(m.rho, m.jx, m.jy, m.e, m.ir);
+  return m;
+}
 
 // One velocity's Lax-Wendroff update with the collision term,
 // f0 + sum_n k_qn (f_n - f0) - C, given the four neighbours' values.  The
@@ -202,7 +223,7 @@ __device__ __forceinline__ P2 expr(P2 x) { return P2(expf(x.v.x), expf(x.v.y)); 
 #define MRTLB_LW_WEIGHTS 0
 #endif
 template <typename R>
-__device__ __forceinline__ R lw_update(const Coef<R>& c, int q, R f0, R Cq, R fE, R fW, R fN, R fS) {
+MRTLB_HD R lw_update(const Coef<R>& c, int q, R f0, R Cq, R fE, R fW, R fN, R fS) {
 #if MRTLB_LW_WEIGHTS
   // (1 - S) f0 - C + sum_n k_qn f_n with S = sum_n k_qn: summed over the
   // nodes of a periodic grid this is sum f0 - sum C exactly whenever S is
@@ -237,7 +258,7 @@ __device__ __forceinline__ double expr(double x) { return exp(x); }
 // Equilibrium moments k = 4..15 (Eqs. 14a-14i and the version rule for
 // k = 11, 14, 15), given the conserved moments and u, T.
 template <typename R>
-__device__ __forceinline__ void equilibrium(const Coef<R>& c, R rho, R inv_rho, R jx, R jy, R e,
+MRTLB_HD void equilibrium(const Coef<R>& c, R rho, R inv_rho, R jx, R jy, R e,
                                             R ux, R uy, R T, R eq[16]) {
   const R ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
   const R p = rho * T;
@@ -351,7 +372,7 @@ MRTLB_HD void inverse_nonconserved(const Coef<R>& c, const R m[16], R f[16]) {
 // state and velocity gradients (dux/dx, dux/dy, duy/dx, duy/dy).
 // collision_h takes the harmonics of f, collision f itself.
 template <typename R>
-__device__ __forceinline__ void collision_h(const Coef<R>& c, const Harm<R>& h, R dux_dx, R dux_dy,
+MRTLB_HD void collision_h(const Coef<R>& c, const Harm<R>& h, R dux_dx, R dux_dy,
                                             R duy_dx, R duy_dy, R rho, R inv_rho, R jx, R jy, R e,
                                             R ux, R uy, R T, R C[16]) {
   R m[16];
@@ -373,7 +394,7 @@ __device__ __forceinline__ void collision_h(const Coef<R>& c, const Harm<R>& h, 
   inverse_nonconserved(c, cc, C);
 }
 template <typename R>
-__device__ __forceinline__ void collision(const Coef<R>& c, const R f[16], R dux_dx, R dux_dy,
+MRTLB_HD void collision(const Coef<R>& c, const R f[16], R dux_dx, R dux_dy,
                                           R duy_dx, R duy_dy, R rho, R inv_rho, R jx, R jy, R e,
                                           R ux, R uy, R T, R C[16]) {
   Harm<R> h;

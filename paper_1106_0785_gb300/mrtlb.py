@@ -38,6 +38,10 @@ MRTLB_KERNEL_AUTO = 0
 MRTLB_KERNEL_PLAIN = 1
 MRTLB_KERNEL_TILED = 2
 
+MRTLB_PEAK_FP32 = 0
+MRTLB_PEAK_FP32_PAIR = 1
+MRTLB_PEAK_FP64 = 2
+
 # every symbol include/mrtlb.h declares (checked by the CPU test suite)
 EXPORTS = (
     "mrtlb_create", "mrtlb_state_bytes", "mrtlb_bind", "mrtlb_init_equilibrium",
@@ -49,7 +53,7 @@ EXPORTS = (
     "mrtlb_batch_get_tiles", "mrtlb_batch_set_graph_steps", "mrtlb_batch_tune", "mrtlb_batch_nodes",
     "mrtlb_batch_last_error", "mrtlb_batch_destroy",
     "mrtlb_set_rates", "mrtlb_get_rates", "mrtlb_selftest_wait", "mrtlb_adjoint_forward", "mrtlb_adjoint_set_interval", "mrtlb_adjoint_backward",
-    "mrtlb_adjoint_release", "mrtlb_equilibrium_adjoint",
+    "mrtlb_adjoint_release", "mrtlb_equilibrium_adjoint", "mrtlb_measure_peak",
 )
 
 MRTLB_NOALLOC_MAX_NODES = 1 << 20
@@ -141,6 +145,7 @@ def load(path=LIB_PATH):
     lib.mrtlb_adjoint_backward.argtypes = [P, P, P, D, P]
     lib.mrtlb_adjoint_release.argtypes = [P]
     lib.mrtlb_equilibrium_adjoint.argtypes = [P] + [P] * 9
+    lib.mrtlb_measure_peak.argtypes = [ctypes.c_int, D]
     _lib = lib
     return lib
 
@@ -244,6 +249,16 @@ def mrtlb_timing_end(ctx):
     n = ctypes.c_long()
     _check(load().mrtlb_timing_end(ctx, ctypes.byref(ms), ctypes.byref(n)), ctx)
     return ms.value, n.value
+
+
+def mrtlb_measure_peak(kind):
+    """Measured fused multiply-add ceiling of the current device in TFLOP/s
+    (MRTLB_PEAK_FP32, MRTLB_PEAK_FP32_PAIR or MRTLB_PEAK_FP64)."""
+    t = ctypes.c_double()
+    rc = load().mrtlb_measure_peak(int(kind), ctypes.byref(t))
+    if rc != MRTLB_OK:
+        raise MrtlbError(rc, "mrtlb_measure_peak(%d)" % kind)
+    return t.value
 
 
 def mrtlb_reduce_noalloc(f, nx, ny, precision, stream=None):
