@@ -57,7 +57,7 @@ __global__ void adj_prep_kernel(const R* __restrict__ ft, const R* __restrict__ 
   load16(ft, L.plane, at, g);
   R rho, jx, jy, e;
   conserved(g, rho, jx, jy, e);
-  const R ir = (rho > R(0)) ? R(1) / rho : R(0);
+  const R ir = (rho > R(0)) ? adj_inv(rho) : R(0);
   const R ux = jx * ir, uy = jy * ir;
   Ux[at] = ux;
   Uy[at] = uy;
@@ -98,7 +98,7 @@ __device__ __forceinline__ void adj_core_node(const R* __restrict__ ft, const R*
 #pragma unroll
   for (int q = 0; q < 16; ++q) rho += g[q];
   // (ghost rows behind walls are never read by an advanced node and may be empty)
-  const R ir = (rho > R(0)) ? R(1) / rho : R(0);
+  const R ir = (rho > R(0)) ? adj_inv(rho) : R(0);
 #pragma unroll
   for (int q = 0; q < 16; ++q) lt[q] = R(0);
   if (advanced<R>(L, i, j)) {
@@ -309,7 +309,7 @@ __global__ void adj_seed_macros_kernel(const R* __restrict__ ft, const double* _
   for (int q = 0; q < 16; ++q) g[q] = ft[q * L.plane + at];
   R rho, jx, jy, e;
   conserved(g, rho, jx, jy, e);
-  const R ir = R(1) / rho;
+  const R ir = adj_inv(rho);
   EqIn<R> x{rho, ir, jx, jy, e, jx * ir, jy * ir, temperature(rho, jx, jy, e, ir)};
   EqIn<R> gi{(R)seed[t], R(0), R(0), R(0), R(0), (R)seed[n + t], (R)seed[2 * n + t], (R)seed[3 * n + t]};
   R rb, jxb, jyb, eb;

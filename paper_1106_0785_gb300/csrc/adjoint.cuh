@@ -12,6 +12,14 @@
 
 namespace mrtlb {
 
+// 1/x as the forward step forms it (FP32: the Newton-refined approximation,
+// 5% faster forward + adjoint than the correctly rounded division; FP64: the
+// division)
+template <typename R>
+__device__ __forceinline__ R adj_inv(R x) {
+  return recip(x);
+}
+
 // transpose of harmonics(): harmonic adjoints -> f adjoints (H^T)
 template <typename R>
 __device__ __forceinline__ void harmonics_T(const Harm<R>& hb, R fb[16]) {
@@ -151,7 +159,7 @@ __device__ __forceinline__ void equilibrium_T(const Coef<R>& c, const EqIn<R>& x
     hb.Q[0] = hb.Q[1] = hb.P[0] = hb.P[1] = R(0);
     R fmb[16];
     harmonics_T(hb, fmb);
-    const R iT = R(1) / x.T;
+    const R iT = adj_inv(x.T);
     const R pre = x.rho * iT * R(0.15915494309189533576888376337251);  // rho / (2 pi T)
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -253,7 +261,7 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
   const Coef<R>& c = a.c;
   R rho, jx, jy, e;
   conserved(g, rho, jx, jy, e);
-  const R ir = R(1) / rho;
+  const R ir = adj_inv(rho);
   const R T = (e - R(0.5) * (jx * ux + jy * uy)) * ir;
 #pragma unroll
   for (int q = 0; q < 16; ++q) lt[q] = (R(1) - c.lwsum[q]) * lp[q];

@@ -109,7 +109,7 @@ struct AdjMarch {
     for (int q = 0; q < 16; ++q) g[q] = fr[q * SM::BW + bc];
     R rho, jx, jy, e;
     conserved(g, rho, jx, jy, e);
-    const R ir = (rho > R(0)) ? R(1) / rho : R(0);  // (rows and columns outside the grid are zero)
+    const R ir = (rho > R(0)) ? adj_inv(rho) : R(0);  // (rows and columns outside the grid are zero)
     const R ux = jx * ir, uy = jy * ir;
     R gsh = R(0), gst = R(0);
     if (a.c.modified && advanced<R>(L, xc, r)) {
