@@ -430,14 +430,14 @@ template <typename R>
 AdjCoef<R> adj_coef(const mrtlb_ctx* c, const Coef<R>& k) {
   AdjCoef<R> a;
   a.c = k;
-  const double dt = c->p.dt, s5 = c->s[4], s6 = c->s[5], s7 = c->s[6], s8 = c->s[7];
-  a.dt = (R)dt;
-  a.g[0] = (R)(dt / s5);
-  a.g[1] = (R)(dt / s6);
-  a.g[2] = (R)(dt * s7 / (s5 * s5));
-  a.g[3] = (R)(dt * s7 / (s6 * s6));
-  a.g[4] = (R)(dt * s8 / (s5 * s5));
-  a.g[5] = (R)(dt * s8 / (s6 * s6));
+  for (int q = 0; q < 16; ++q) a.selfw[q] = R(1) - k.lwsum[q];
+  const double s5 = c->s[4], s6 = c->s[5], s7 = c->s[6], s8 = c->s[7];
+  a.g[0] = (R)(1.0 / s5);
+  a.g[1] = (R)(1.0 / s6);
+  a.g[2] = (R)(s7 / (s5 * s5));
+  a.g[3] = (R)(s7 / (s6 * s6));
+  a.g[4] = (R)(s8 / (s5 * s5));
+  a.g[5] = (R)(s8 / (s6 * s6));
   return a;
 }
 
@@ -595,6 +595,8 @@ int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, 
   ACK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, st), "read error word");
   ACK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   if (h & ERRBIT_TIMEOUT) return afail(c, MRTLB_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (dL_ds)  // the kernels sum the rate gradients without the factor dt
+    for (int k = 0; k < 16; ++k) dL_ds[k] *= c->p.dt;
   return MRTLB_OK;
 }
 

@@ -204,9 +204,10 @@ __device__ __forceinline__ void chain_primitive(const EqIn<R>& x, const EqIn<R>&
 template <typename R>
 struct AdjCoef {
   Coef<R> c;
-  R dt;
-  // derivatives of the modification factors dt (s7/s5 - 1), ... :
-  // dt/s5, dt/s6, dt s7/s5^2, dt s7/s6^2, dt s8/s5^2, dt s8/s6^2
+  R selfw[16];  // Lax-Wendroff self weight 1 - sum_n k_qn, in R as the step forms it
+  // derivatives of the modification factors dt (s7/s5 - 1), ... divided by
+  // dt (the rate gradients are summed without the factor dt, which the host
+  // applies to the totals): 1/s5, 1/s6, s7/s5^2, s7/s6^2, s8/s5^2, s8/s6^2
   R g[6];
 };
 
@@ -264,7 +265,7 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
   const R ir = adj_inv(rho);
   const R T = (e - R(0.5) * (jx * ux + jy * uy)) * ir;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) lt[q] = (R(1) - c.lwsum[q]) * lp[q];
+  for (int q = 0; q < 16; ++q) lt[q] = a.selfw[q] * lp[q];
   Harm<R> h;
   harmonics(g, h);
   R m[16], eq[16];
@@ -304,18 +305,17 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
   harmonics_T(hb, fb);
 #pragma unroll
   for (int q = 0; q < 16; ++q) lt[q] += fb[q];
-  // rate gradients: d f1 / d s_k through dt s_k (m_k - eq_k) and the
-  // modification factors dt (s7/s5 - 1), ... (dL/dC = -lambda)
-  const R dt = a.dt;
+  // rate gradients over dt: d f1 / d s_k through dt s_k (m_k - eq_k) and
+  // the modification factors dt (s7/s5 - 1), ... (dL/dC = -lambda)
 #pragma unroll
-  for (int k = 4; k < 16; ++k) G[k] += dt * cb[k] * (m[k] - eq[k]);
+  for (int k = 4; k < 16; ++k) G[k] += cb[k] * (m[k] - eq[k]);
   if (c.modified) {
     const R A0 = Pp * ux * shear, A1 = Pp * uy * strain;
     const R A2 = Pp * ux * strain, A3 = Pp * uy * shear;
-    G[6] += cb[6] * (A0 * a.g[0] + A1 * a.g[1]);        // dt/s5, dt/s6
+    G[6] += cb[6] * (A0 * a.g[0] + A1 * a.g[1]);        // 1/s5, 1/s6
     G[7] += cb[7] * (A2 * a.g[1] + A3 * a.g[0]);
-    G[4] -= cb[6] * A0 * a.g[2] + cb[7] * A3 * a.g[4];  // dt s7/s5^2, dt s8/s5^2
-    G[5] -= cb[6] * A1 * a.g[3] + cb[7] * A2 * a.g[5];  // dt s7/s6^2, dt s8/s6^2
+    G[4] -= cb[6] * A0 * a.g[2] + cb[7] * A3 * a.g[4];  // s7/s5^2, s8/s5^2
+    G[5] -= cb[6] * A1 * a.g[3] + cb[7] * A2 * a.g[5];  // s7/s6^2, s8/s6^2
   }
 }
 
