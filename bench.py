@@ -20,6 +20,8 @@ Printed JSON line (rank 0):
   fp64_mlups the all-FP64 path on the same input
   compute    the step's flop rate (counted flops per node update) against
              fused multiply-add ceilings measured on the device
+  small      microseconds per step of the latency-bound small configurations
+             (Sod 400 x 4 FP64, Couette 4 x 200 FP64 and FP32)
   cpu_baseline  the FP64 numpy oracle on a crop of the same input, one thread
 
 Multi-GPU (torchrun): every rank advances its own replica (weak scaling, no
@@ -400,6 +402,9 @@ def run_mine(args, world, rank, local):
     if not args.no_batch:
         batched = run_batched(args, world, dev)
 
+    # ---- the small, latency-bound configurations ----------------------------
+    small = run_small(dev)
+
     if rank != 0:
         return
     line = {
@@ -419,6 +424,7 @@ def run_mine(args, world, rank, local):
         "fp64_ms_per_step": ms64 / args.fp64_steps,
         "batched": batched,
         "fwd_adj": fwd_adj,
+        "small": small,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -464,6 +470,37 @@ def run_fwd_adj(args, world, dev, cfg, fields, nodes):
             "mlups": world * nodes * K / el / 1e6, "seconds": el,
             "algorithmic_gbs": gbs, "frac_of_hbm": gbs / peak,
             "dL_ds_visc": float(ds[4] + ds[5]), "dL_ds_cond": float(ds[6] + ds[7])}
+
+
+def run_small(dev):
+    """Microseconds per step of the two small configurations, which launch
+    latency rather than HBM bounds: the Sod tube (400 x 4, FP64, its 1500
+    steps to t = 0.015) and thermal Couette flow (4 x 200, FP64 and FP32,
+    2000 steps), each as the library's graph-replayed time loop after a
+    warm-up."""
+    import torch
+
+    from paper_1106_0785_gb300 import workloads
+    from paper_1106_0785_gb300.simulation import Simulation
+
+    out = {}
+    for name, (cfg, fields), steps in (
+            ("sod_400x4_fp64", workloads.sod(precision="fp64"), 1500),
+            ("couette_4x200_fp64", workloads.couette(Pr=2.0, precision="fp64"), 2000),
+            ("couette_4x200_fp32", workloads.couette(Pr=2.0, precision="fp32"), 2000)):
+        with Simulation(cfg, device=dev) as sim:
+            sim.init_equilibrium(*fields)
+            sim.step(128)
+            sim.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(sim.stream)
+            sim.step(steps)
+            e1.record(sim.stream)
+            torch.cuda.synchronize(dev)
+            sim.sync()
+            out[name + "_us_per_step"] = 1e3 * e0.elapsed_time(e1) / steps
+    return out
 
 
 def run_batched(args, world, dev):
