@@ -22,12 +22,18 @@ __device__ __forceinline__ void node_velocity(const R* __restrict__ f, long long
   uy = jy * r;
 }
 
+// Thread t takes advanced node t of the row-major enumeration of
+// [i0, i1) x [j0, j1), so that every lane of a warp has a node whatever the
+// grid's shape (a 4-column grid would leave 28 of 32 lanes idle under a
+// 2D block, and FP64 arithmetic costs a warp the same with idle lanes).
 template <typename R>
 __global__ void __launch_bounds__(128) step_plain_kernel(const R* __restrict__ fin, R* __restrict__ fout,
                                                          Layout L, Coef<R> c, int* err) {
-  const int i = L.i0 + blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = L.j0 + blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= L.i1 || j >= L.j1) return;
+  const int ni = L.i1 - L.i0;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ni * (L.j1 - L.j0)) return;
+  const int i = L.i0 + (int)(t % ni);
+  const int j = L.j0 + (int)(t / ni);
   const long long P = L.plane;
   const long long at = L.node(i, j);
   const long long E = at + 1, W = at - 1, N = at + L.pitch, S = at - L.pitch;
@@ -71,9 +77,19 @@ void launch_step_plain(const R* fin, R* fout, const Layout& L, const Coef<R>& c,
                        cudaStream_t st) {
   const int ni = L.i1 - L.i0, nj = L.j1 - L.j0;
   if (ni <= 0 || nj <= 0) return;
-  dim3 blk(32, 4);
-  dim3 grd((ni + 31) / 32, (nj + 3) / 4);
-  step_plain_kernel<R><<<grd, blk, 0, st>>>(fin, fout, L, c, err);
+  // a grid small enough to leave SMs idle takes blocks of fewer threads
+  // (the smallest power of two, at least 8, that covers it with one block
+  // per SM), so that its latency-bound nodes spread over every SM
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+  }
+  const long long n = (long long)ni * nj;
+  int blk = 8;
+  while (blk < 128 && (long long)blk * nsm < n) blk *= 2;
+  step_plain_kernel<R><<<(unsigned)((n + blk - 1) / blk), blk, 0, st>>>(fin, fout, L, c, err);
 }
 
 // ---------------------------------------------------------------------------
