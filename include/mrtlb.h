@@ -324,6 +324,21 @@ int mrtlb_equilibrium_adjoint(mrtlb_ctx* ctx, const double* dL_df, const double*
                               const double* ux, const double* uy, const double* T,
                               double* dL_drho, double* dL_dux, double* dL_duy, double* dL_dT);
 
+/* Checkpoint and resume.  mrtlb_save writes the current state to a file
+ * (a header with the grid, precision, step count and a hash of every
+ * parameter the step depends on, the dense state [16][ny][nx] in the
+ * state's precision, and a checksum), through a sibling file that replaces
+ * path only once it is complete; it synchronises.  mrtlb_load reads such a
+ * file into a bound context with the same parameters (grid, spacings, time
+ * step, current rates, equilibrium version, modification, precision and
+ * sides) and restores the step count; a run resumed from the checkpoint of
+ * step n continues bitwise as the original run.  Returns MRTLB_ERR_ARG for
+ * an unreadable, truncated or corrupted file (checksum), another grid,
+ * precision or parameter set, or an I/O failure, leaving the context as it
+ * was. */
+int mrtlb_save(mrtlb_ctx* ctx, const char* path);
+int mrtlb_load(mrtlb_ctx* ctx, const char* path);
+
 /* Number of time steps taken since the last init/set. */
 long mrtlb_step_count(const mrtlb_ctx* ctx);
 

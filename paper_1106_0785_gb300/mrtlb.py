@@ -54,6 +54,7 @@ EXPORTS = (
     "mrtlb_batch_last_error", "mrtlb_batch_destroy",
     "mrtlb_set_rates", "mrtlb_get_rates", "mrtlb_selftest_wait", "mrtlb_adjoint_forward", "mrtlb_adjoint_set_interval", "mrtlb_adjoint_backward",
     "mrtlb_adjoint_release", "mrtlb_equilibrium_adjoint", "mrtlb_measure_peak",
+    "mrtlb_save", "mrtlb_load",
 )
 
 MRTLB_NOALLOC_MAX_NODES = 1 << 20
@@ -146,6 +147,8 @@ def load(path=LIB_PATH):
     lib.mrtlb_adjoint_release.argtypes = [P]
     lib.mrtlb_equilibrium_adjoint.argtypes = [P] + [P] * 9
     lib.mrtlb_measure_peak.argtypes = [ctypes.c_int, D]
+    lib.mrtlb_save.argtypes = [P, ctypes.c_char_p]
+    lib.mrtlb_load.argtypes = [P, ctypes.c_char_p]
     _lib = lib
     return lib
 
@@ -249,6 +252,16 @@ def mrtlb_timing_end(ctx):
     n = ctypes.c_long()
     _check(load().mrtlb_timing_end(ctx, ctypes.byref(ms), ctypes.byref(n)), ctx)
     return ms.value, n.value
+
+
+def mrtlb_save(ctx, path):
+    """Write the context's state to a checkpoint file (synchronises)."""
+    _check(load().mrtlb_save(ctx, os.fsencode(path)), ctx)
+
+
+def mrtlb_load(ctx, path):
+    """Resume the context from a checkpoint written with the same parameters."""
+    _check(load().mrtlb_load(ctx, os.fsencode(path)), ctx)
 
 
 def mrtlb_measure_peak(kind):

@@ -63,6 +63,14 @@ class Simulation:
         M.mrtlb_get_f(self.ctx, out, on_device)
         return out
 
+    def save(self, path):
+        """Checkpoint the state (and the step count) to a file."""
+        M.mrtlb_save(self.ctx, path)
+
+    def load(self, path):
+        """Resume from a checkpoint written with the same configuration."""
+        M.mrtlb_load(self.ctx, path)
+
     def macros(self, on_device=False):
         shape = (self.cfg.ny, self.cfg.nx)
         if on_device:
