@@ -531,6 +531,7 @@ const Coef<R>& coef_of(const mrtlb_ctx* c) {
 // into `last` unless it is null (then the segment's final state is not kept).
 template <typename R>
 void run_segment(mrtlb_ctx* c, mrtlb_adjoint_state* a, long len, const Coef<R>& k, cudaStream_t st, R* last) {
+  TraceRange trace_("adjoint_segment");
   for (long n = 0; n < len; ++n) {
     R* fin = slot<R>(c, a, n);
     launch_walls<R>(fin, c->L, coef_of<R>(c), c->walls, st);
@@ -704,6 +705,7 @@ extern "C" int mrtlb_adjoint_set_interval(mrtlb_ctx* c, long S) {
 }
 
 extern "C" int mrtlb_adjoint_forward(mrtlb_ctx* c, long K) {
+  TraceRange trace_("mrtlb_adjoint_forward");
   if (!c) return MRTLB_ERR_ARG;
   if (!c->f[0] || !c->f[1]) return afail(c, MRTLB_ERR_STATE, "bind state buffers first");
   if (K < 0) return afail(c, MRTLB_ERR_ARG, "K < 0");
@@ -712,6 +714,7 @@ extern "C" int mrtlb_adjoint_forward(mrtlb_ctx* c, long K) {
 
 extern "C" int mrtlb_adjoint_backward(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK,
                                       double dL_ds[16], double* dL_df0) {
+  TraceRange trace_("mrtlb_adjoint_backward");
   if (!c) return MRTLB_ERR_ARG;
   if (!c->adj) return afail(c, MRTLB_ERR_STATE, "call mrtlb_adjoint_forward first");
   if (!dL_dmacros && !dL_dfK) return afail(c, MRTLB_ERR_ARG, "a seed (dL/dmacros or dL/df^K) is required");

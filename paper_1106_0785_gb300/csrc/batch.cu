@@ -523,6 +523,7 @@ extern "C" int mrtlb_batch_set_graph_steps(mrtlb_batch* b, int steps) {
 }
 
 extern "C" int mrtlb_batch_step(mrtlb_batch* b, long nsteps) {
+  TraceRange trace_("mrtlb_batch_step");
   if (!b || nsteps < 0) return MRTLB_ERR_ARG;
   for (mrtlb_ctx* c : b->ctx)
     if (c->cur != b->cur) return bfail(b, MRTLB_ERR_STATE, "an instance was stepped or reset outside the batch");

@@ -78,6 +78,7 @@ bool take(FILE* fh, T* v) {
 }  // namespace
 
 extern "C" int mrtlb_save(mrtlb_ctx* c, const char* path) {
+  TraceRange trace_("mrtlb_save");
   if (!c) return MRTLB_ERR_ARG;
   if (!path || !path[0]) return ck_fail(c, MRTLB_ERR_ARG, "no checkpoint path");
   const size_t bytes = (size_t)16 * c->L.nx * c->L.ny * c->esize;
@@ -111,6 +112,7 @@ extern "C" int mrtlb_save(mrtlb_ctx* c, const char* path) {
 }
 
 extern "C" int mrtlb_load(mrtlb_ctx* c, const char* path) {
+  TraceRange trace_("mrtlb_load");
   if (!c) return MRTLB_ERR_ARG;
   if (!path || !path[0]) return ck_fail(c, MRTLB_ERR_ARG, "no checkpoint path");
   FILE* fh = std::fopen(path, "rb");

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 
 #include "../../include/mrtlb.h"
@@ -10,6 +12,15 @@
 #include "step_tiled.cuh"
 
 using namespace mrtlb;
+
+// A named range on a profiler's host timeline around one library call
+// (NVTX; nothing is recorded unless a tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 struct mrtlb_adjoint_state;  // adjoint.cu
 

@@ -405,6 +405,7 @@ static bool bound(mrtlb_ctx* c) { return c && c->f[0] && c->f[1]; }
 // The boundary fill of f; the fixed inflow ghosts go into both state
 // buffers, since a step writes every other ghost of its output itself.
 static void enqueue_bc(mrtlb_ctx* c, void* f) {
+  TraceRange trace_("bc_fill");
   if (c->prec == MRTLB_FP64) launch_bc<double>((double*)f, c->L, c->c64, c->walls, c->stream);
   else launch_bc<float>((float*)f, c->L, c->c32, c->walls, c->stream);
   for (int b = 0; b < 2; ++b) {
@@ -519,6 +520,7 @@ static int enqueue_steps(mrtlb_ctx* c, long nsteps) {
 }
 
 extern "C" int mrtlb_step(mrtlb_ctx* c, long nsteps) {
+  TraceRange trace_("mrtlb_step");
   if (!bound(c)) return c ? fail(c, MRTLB_ERR_STATE, "bind state buffers first") : MRTLB_ERR_ARG;
   if (nsteps < 0) return fail(c, MRTLB_ERR_ARG, "nsteps < 0");
   return enqueue_steps(c, nsteps);
@@ -553,6 +555,7 @@ extern "C" int mrtlb_selftest_wait(mrtlb_ctx* c) {
 }
 
 extern "C" int mrtlb_macros(mrtlb_ctx* c, double* rho, double* ux, double* uy, double* T, int on_device) {
+  TraceRange trace_("mrtlb_macros");
   if (!bound(c)) return c ? fail(c, MRTLB_ERR_STATE, "bind state buffers first") : MRTLB_ERR_ARG;
   const size_t n = (size_t)c->L.nx * c->L.ny;
   void* f = c->f[c->cur];
@@ -580,6 +583,7 @@ extern "C" int mrtlb_macros(mrtlb_ctx* c, double* rho, double* ux, double* uy, d
 }
 
 extern "C" int mrtlb_reduce(mrtlb_ctx* c, double out[5]) {
+  TraceRange trace_("mrtlb_reduce");
   if (!bound(c)) return c ? fail(c, MRTLB_ERR_STATE, "bind state buffers first") : MRTLB_ERR_ARG;
   if (!out) return fail(c, MRTLB_ERR_ARG, "out is NULL");
   const size_t n = (size_t)c->L.nx * c->L.ny;
@@ -598,6 +602,7 @@ extern "C" int mrtlb_reduce(mrtlb_ctx* c, double out[5]) {
 }
 
 extern "C" int mrtlb_get_f(mrtlb_ctx* c, void* f, int on_device) {
+  TraceRange trace_("mrtlb_get_f");
   if (!bound(c)) return c ? fail(c, MRTLB_ERR_STATE, "bind state buffers first") : MRTLB_ERR_ARG;
   if (!f) return fail(c, MRTLB_ERR_ARG, "f is NULL");
   const size_t bytes = (size_t)16 * c->L.nx * c->L.ny * c->esize;
@@ -621,6 +626,7 @@ extern "C" int mrtlb_get_f(mrtlb_ctx* c, void* f, int on_device) {
 }
 
 extern "C" int mrtlb_set_f(mrtlb_ctx* c, const void* f, int on_device) {
+  TraceRange trace_("mrtlb_set_f");
   if (!bound(c)) return c ? fail(c, MRTLB_ERR_STATE, "bind state buffers first") : MRTLB_ERR_ARG;
   if (!f) return fail(c, MRTLB_ERR_ARG, "f is NULL");
   const size_t bytes = (size_t)16 * c->L.nx * c->L.ny * c->esize;
