@@ -23,6 +23,8 @@ Printed JSON line (rank 0):
   small      microseconds per step of the latency-bound small configurations
              (Sod 400 x 4 FP64, Couette 4 x 200 FP64 and FP32)
   cpu_baseline  the FP64 numpy oracle on a crop of the same input, one thread
+  oracle_parity the FP32 CUDA path on that crop after the same steps, against
+                the oracle's result (largest errors in rho, u, T)
 
 Multi-GPU (torchrun): every rank advances its own replica (weak scaling, no
 data-path collective); the max time over ranks is reported.
@@ -224,34 +226,78 @@ def _crop_problem(crop):
     return p, oeq.feq(rho[sl], ux[sl], uy[sl], T[sl])
 
 
-def cpu_baseline_worker(seconds):
+def cpu_baseline_worker(seconds, out=None):
+    import numpy as np
+
     from oracle import fdlb
-    p, f = _crop_problem(CROP)
-    f = fdlb.step(f, p)  # warm-up
-    n, t0 = 0, time.perf_counter()
+    p, f0 = _crop_problem(CROP)
+    f = fdlb.step(f0, p)  # warm-up (counted: the result is compared step for step)
+    n, t0 = 1, time.perf_counter()
     while True:
         f = fdlb.step(f, p)
         n += 1
         el = time.perf_counter() - t0
         if (el >= seconds and n >= 3) or n >= 100000:
             break
-    print(json.dumps({"steps": n, "seconds": el, "nodes": p.nx * p.ny}))
+    if out:
+        np.savez(out, f0=f0, fn=f)
+    print(json.dumps({"steps": n, "timed_steps": n - 1, "seconds": el, "nodes": p.nx * p.ny}))
 
 
-def cpu_baseline(seconds):
+def cpu_baseline(seconds, dev=None):
+    """The oracle's rate on the crop (one thread, in a subprocess), and, when
+    a device is given, the CUDA path's error against the oracle's result on
+    that same crop after the same number of steps (FP32, the bench's
+    precision): returns (cpu_baseline, oracle_parity)."""
+    import tempfile
+
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = "import bench; bench.cpu_baseline_worker(%r)" % seconds
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
-                       text=True, timeout=600)
-    if r.returncode != 0:
-        return {"error": r.stderr[-300:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    mlups = d["nodes"] * d["steps"] / d["seconds"] / 1e6
+    with tempfile.TemporaryDirectory() as tmp:
+        out = os.path.join(tmp, "oracle_crop.npz")
+        code = "import bench; bench.cpu_baseline_worker(%r, %r)" % (seconds, out)
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                           text=True, timeout=600)
+        if r.returncode != 0:
+            return {"error": r.stderr[-300:]}, None
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        parity = crop_parity(out, d["steps"], dev) if dev is not None else None
+    mlups = d["nodes"] * d["timed_steps"] / d["seconds"] / 1e6
     x0, y0, nx, ny = CROP
-    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    base = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": "FP64 numpy oracle, %d steps of a %dx%d crop (x %d-%d, y %d-%d) of the "
                       "Richtmyer-Meshkov 4096x1024 initial state, one thread, %.1f s"
-                      % (d["steps"], nx, ny, x0, x0 + nx - 1, y0, y0 + ny - 1, d["seconds"])}
+                      % (d["timed_steps"], nx, ny, x0, x0 + nx - 1, y0, y0 + ny - 1, d["seconds"])}
+    return base, parity
+
+
+def crop_parity(path, steps, dev):
+    """The FP32 CUDA path on the oracle's crop problem (outflow in x,
+    periodic in y), from the same initial state for the same steps: the
+    largest relative error in rho and T and in u relative to max |u|."""
+    import numpy as np
+
+    from oracle import fdlb
+    from paper_1106_0785_gb300 import mrtlb as M
+    from paper_1106_0785_gb300 import workloads
+    from paper_1106_0785_gb300.simulation import Simulation
+
+    z = np.load(path)
+    cfg, _ = workloads.richtmyer_meshkov(nx=NX, ny=NY)
+    x0, y0, nx, ny = CROP
+    crop = M.Config(nx=nx, ny=ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt, s=cfg.s,
+                    bc=(("outflow", 0, 0, 1),) * 2 + (("periodic", 0, 0, 1),) * 2,
+                    eq_version=cfg.eq_version, modified=cfg.modified, precision="fp32")
+    with Simulation(crop, device=dev) as sim:
+        sim.set_f(z["f0"].astype(np.float32))
+        sim.step(steps)
+        r, ux, uy, T = sim.macros()
+    r0, ux0, uy0, T0 = fdlb.macros(z["fn"])
+    umax = max(np.abs(ux0).max(), np.abs(uy0).max())
+    return {"steps": int(steps), "precision": "fp32", "against": "the FP64 oracle",
+            "sample": "the cpu_baseline crop",
+            "max_rel_err_rho": float((np.abs(r - r0) / np.abs(r0)).max()),
+            "max_err_u_over_umax": float(max(np.abs(ux - ux0).max(), np.abs(uy - uy0).max()) / umax),
+            "max_rel_err_T": float((np.abs(T - T0) / np.abs(T0)).max())}
 
 
 # ---------------------------------------------------------------------------
@@ -277,7 +323,9 @@ def run_reference(args, world, rank):
         "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "richtmyer_meshkov_4096x1024", "sample": sample},
+        "config": {"workload": "richtmyer_meshkov_4096x1024", "nx": NX, "ny": NY,
+                   "precision": "fp64 (the oracle)", "parallelism": "host cores, one thread",
+                   "sample": sample},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -428,7 +476,7 @@ def run_mine(args, world, rank, local):
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"], line["oracle_parity"] = cpu_baseline(args.cpu_seconds, dev)
     print(json.dumps(line), flush=True)
 
 
