@@ -70,6 +70,8 @@ struct AdjMarch {
   Layout L;
   int t, x0, x, boxx, r_first, r_last, f_issued, l_issued;
   bool out_col;  // the thread's column is an output of this strip
+  bool colC, colW, colE;  // columns x, x-1, x+1 are advanced (fixed per segment)
+  __device__ __forceinline__ bool row_adv(int r) const { return r >= L.j0 && r < L.j1; }
 
   __device__ __forceinline__ int k(int r) const { return r - r_first; }
   __device__ __forceinline__ const R* frow(int r) const { return fs + (k(r) % NF) * SM::ROW; }
@@ -112,7 +114,7 @@ struct AdjMarch {
     const R ir = (rho > R(0)) ? adj_inv(rho) : R(0);  // (rows and columns outside the grid are zero)
     const R ux = jx * ir, uy = jy * ir;
     R gsh = R(0), gst = R(0);
-    if (a.c.modified && advanced<R>(L, xc, r)) {
+    if (a.c.modified && colC && row_adv(r)) {  // (xc is the thread's own column x)
       R lam[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) lam[q] = lr[q * SM::BW + bc];
@@ -145,7 +147,8 @@ struct AdjMarch {
     R lt[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) lt[q] = R(0);
-    if (advanced<R>(L, x, j)) {
+    const bool rC = row_adv(j);
+    if (colC && rC) {
       const R* fr = frow(j);
       R g[16], lp[16];
 #pragma unroll
@@ -158,8 +161,8 @@ struct AdjMarch {
       collision_T_node(a, g, lp, ux, uy, shear, strain, lt, G);
     }
     // neighbours' Lax-Wendroff weights: r = p - e_x (k_E), p + e_x (k_W), p - e_y (k_N), p + e_y (k_S)
-    const bool aW = advanced<R>(L, x - 1, j), aE = advanced<R>(L, x + 1, j);
-    const bool aS = advanced<R>(L, x, j - 1), aN = advanced<R>(L, x, j + 1);
+    const bool aW = colW && rC, aE = colE && rC;
+    const bool aS = colC && row_adv(j - 1), aN = colC && row_adv(j + 1);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       if (vx_of(q) != 0) {
@@ -190,6 +193,9 @@ struct AdjMarch {
   __device__ __forceinline__ bool segment(const AdjCoef<R>& a, int ja, int jb, R G[16]) {
     x = x0 - 2 + t;
     out_col = t >= 1 && t <= SM::SX && x <= L.nx;
+    colC = x >= L.i0 && x < L.i1;
+    colW = x - 1 >= L.i0 && x - 1 < L.i1;
+    colE = x + 1 >= L.i0 && x + 1 < L.i1;
     boxx = L.xoff + x0 - SM::HL;
     r_first = ja - 1;
     r_last = jb;
