@@ -22,4 +22,7 @@ couette      closed-form thermal Couette temperature profile (Sec. IV A)
 Every function works on numpy arrays of float64; the step also accepts
 complex128 so that a complex-step derivative (Squire & Trapp 1998) gives the
 exact tangent of the step.
+
+Parity unpinned: equilibrium version 2 (see ``equilibrium``); every other
+function is pinned by the tests in ``tests/test_oracle_*.py``.
 """

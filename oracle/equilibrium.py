@@ -13,6 +13,13 @@ Eq. 5):
 
 All functions broadcast over arrays of any shape and accept complex input
 (complex-step differentiation).
+
+Parity unpinned: the version-2 formulas.  The paper derives them from the
+requirement that the model reduce to an earlier single-relaxation-time model
+(Chen 1994), which is not part of the paper, so they are pinned only as the
+text states them; they still leave the conserved moments untouched and the
+collision conserving.  Versions 1 and 3 are pinned (version 3 against the
+discrete Maxwellian's moments).
 """
 import numpy as np
 

@@ -80,6 +80,20 @@ def test_version_rules():
     assert abs((M[14] * fmax).sum()) < 1e-14 and abs((M[15] * fmax).sum()) < 1e-14
 
 
+def test_version3_at_rest_is_the_closed_form_of_row_12():
+    """At u = 0 the sampled Maxwellian of version 3 is rho/(2 pi T)
+    exp(-|v|^2 / 2T) on every velocity of a shell, and row 12 of the printed
+    M weighs the shells (|v|^2 = 1, 2, 4, 8) by 1, -4, 16, -64: so
+    f^12 = 4 rho / (2 pi T) sum_s w_s exp(-|v_s|^2 / 2T), and rows 15, 16
+    (odd in v) vanish."""
+    for rho, T in ((1.0, 1.0), (2.5, 0.6), (0.4, 3.0)):
+        v3 = eq.feq_hat(np.array(rho), np.array(0.0), np.array(0.0), np.array(rho * T), version=3)
+        want = 4.0 * rho / (2.0 * np.pi * T) * sum(w * np.exp(-r2 / (2.0 * T))
+                                                   for w, r2 in ((1, 1), (-4, 2), (16, 4), (-64, 8)))
+        assert np.isclose(v3[11], want, rtol=1e-13, atol=1e-15)
+        assert abs(v3[14]) < 1e-14 and abs(v3[15]) < 1e-14
+
+
 def test_primitive_inverts_conserved():
     rho, ux, uy, T = 0.7, -1.2, 0.3, 2.5
     e = rho * (T + 0.5 * (ux * ux + uy * uy))
