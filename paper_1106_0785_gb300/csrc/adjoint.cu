@@ -446,12 +446,11 @@ void launch_adj_march(const mrtlb_adjoint_state* a, const Layout& L, const CUten
                       R* out, const AdjCoef<R>& ac, int* err, cudaStream_t st) {
   constexpr int BX = AdjTile<R>::BX, NF = AdjTile<R>::NF, NL = AdjTile<R>::NL;
   using SM = AdjSmem<R, BX, NF, NL>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)SM::bytes);
-    attr = true;
-  }
+  static const bool attr = [] {  // once per instantiation (thread-safe static initialisation)
+    return cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SM::bytes) == cudaSuccess;
+  }();
+  (void)attr;
   dim3 grid(a->m_nstrips, a->m_nseg);
   adj_march_kernel<R, BX, NF, NL><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
 }

@@ -209,21 +209,21 @@ template <typename R, int BX, int MINB>
 void launch_batched_bx(const void* insts, const int4* tiles, int ntiles, int grid, int cur, int* err, int* claim,
                        cudaStream_t st) {
   constexpr int NS = BatchShapes<R>::NS;
-  static bool attr = false;
   if constexpr (sizeof(R) == 4 && MRTLB_PAIR) {
-    if (!attr) {
-      cudaFuncSetAttribute(step_batched_pair_kernel<BX, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)batch_pair_smem<BX, NS>());
-      attr = true;
-    }
+    static const bool attr = [] {  // once per instantiation (thread-safe static initialisation)
+      return cudaFuncSetAttribute(step_batched_pair_kernel<BX, NS, MINB>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)batch_pair_smem<BX, NS>()) == cudaSuccess;
+    }();
+    (void)attr;
     step_batched_pair_kernel<BX, NS, MINB><<<grid, BX / 2, batch_pair_smem<BX, NS>(), st>>>(
         (const BatchInst<float>*)insts, tiles, ntiles, cur, err, claim);
   } else {
-    if (!attr) {
-      cudaFuncSetAttribute(step_batched_kernel<R, BX, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)batch_smem<R, BX, NS>());
-      attr = true;
-    }
+    static const bool attr = [] {
+      return cudaFuncSetAttribute(step_batched_kernel<R, BX, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)batch_smem<R, BX, NS>()) == cudaSuccess;
+    }();
+    (void)attr;
     step_batched_kernel<R, BX, NS, MINB><<<grid, BX, batch_smem<R, BX, NS>(), st>>>(
         (const BatchInst<R>*)insts, tiles, ntiles, cur, err);
   }

@@ -80,12 +80,12 @@ void launch_step_plain(const R* fin, R* fout, const Layout& L, const Coef<R>& c,
   // a grid small enough to leave SMs idle takes blocks of fewer threads
   // (the smallest power of two, at least 8, that covers it with one block
   // per SM), so that its latency-bound nodes spread over every SM
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
+  static const int nsm = [] {  // thread-safe static initialisation
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
-  }
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    return n;
+  }();
   const long long n = (long long)ni * nj;
   int blk = 8;
   while (blk < 128 && (long long)blk * nsm < n) blk *= 2;

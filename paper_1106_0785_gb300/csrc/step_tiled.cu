@@ -108,17 +108,15 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeFn get_encode() {
-  static EncodeFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const EncodeFn fn = [] {  // thread-safe static initialisation
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeFn)p;
-  }
+      return (EncodeFn)p;
+    return (EncodeFn) nullptr;
+  }();
   return fn;
 }
 
@@ -247,22 +245,20 @@ void launch_step_tiled(const TiledPlan& plan, int cur, const Layout& L, const Co
   dim3 grd(plan.nstrips, plan.nseg);
   if constexpr (sizeof(R) == 4 && MRTLB_PAIR) {
     using SM = PairSmem<BX, NS>;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(step_pair_kernel<BX, NS, MRTLB_PAIR_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SM::bytes);
-      attr = true;
-    }
+    static const bool attr = [] {  // once per instantiation (thread-safe static initialisation)
+      return cudaFuncSetAttribute(step_pair_kernel<BX, NS, MRTLB_PAIR_MINB>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes) == cudaSuccess;
+    }();
+    (void)attr;
     step_pair_kernel<BX, NS, MRTLB_PAIR_MINB><<<grd, BX / 2, SM::bytes, st>>>(
         plan.map[cur], (float*)fout, L, pair_coef(reinterpret_cast<const Coef<float>&>(c)), err, plan.seglen);
   } else {
     using SM = Smem<R, BX, NS>;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(step_tiled_kernel<R, BX, NS, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SM::bytes);
-      attr = true;
-    }
+    static const bool attr = [] {
+      return cudaFuncSetAttribute(step_tiled_kernel<R, BX, NS, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SM::bytes) == cudaSuccess;
+    }();
+    (void)attr;
     step_tiled_kernel<R, BX, NS, MB><<<grd, BX, SM::bytes, st>>>(plan.map[cur], (R*)fout, L, c, err,
                                                                  plan.seglen);
   }
