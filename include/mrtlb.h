@@ -30,6 +30,10 @@
  *   mrtlb_set_f).
  * - Dense field layouts: a scalar field is [ny][nx] (x fastest); the
  *   distributions are [16][ny][nx], plane q = the paper's velocity i = q+1.
+ * - Threads: calls on one context (or one batch, with its instances) must not
+ *   overlap; different contexts may be driven from different host threads at
+ *   the same time.  mrtlb_last_error(NULL) reports the calling thread's
+ *   last failed mrtlb_create.
  */
 #ifndef MRTLB_H
 #define MRTLB_H
@@ -343,7 +347,8 @@ int mrtlb_load(mrtlb_ctx* ctx, const char* path);
 long mrtlb_step_count(const mrtlb_ctx* ctx);
 
 /* Message of the last error on ctx (never NULL; "" if none).  With
- * ctx == NULL it returns the last error of a failed mrtlb_create. */
+ * ctx == NULL it returns the message of the calling thread's last failed
+ * mrtlb_create. */
 const char* mrtlb_last_error(const mrtlb_ctx* ctx);
 
 /* Release the context and the scratch it owns (not the bound buffers). */
