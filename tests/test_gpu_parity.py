@@ -118,22 +118,45 @@ def test_fp64_init_equilibrium_matches_oracle(cuda):
         assert np.abs(x - y).max() < 1e-13 * max(1.0, np.abs(y).max())
 
 
-def test_fp32_smooth_flow_1000_steps(cuda):
-    """FP32 storage and arithmetic (compensated temperature numerator) vs the FP64 oracle."""
-    cfg = _cfg(160, 44, BCS["periodic"], "fp32", dt=1e-4)
+_ORACLE_RUNS = {}
+
+
+def _oracle_run(key, f0, p, n):
+    """The oracle's n steps, shared by the kernels compared with it."""
+    if key not in _ORACLE_RUNS:
+        _ORACLE_RUNS[key] = fdlb.macros(fdlb.run(f0, p, n))
+    return _ORACLE_RUNS[key]
+
+
+# Version 2 (parity unpinned in the oracle: its formulas are pinned only as
+# the text states them) carries 10 T and 5 u^2 terms in moments 15 and 16 that
+# the other versions set to zero or to the Maxwellian's small values; its
+# larger collision terms leave 1.0e-5 of max |u| after 1000 FP32 steps on the
+# row-march kernel (measured), so it is held to 2e-5 in u.
+U_BOUND = {1: 1e-5, 2: 2e-5, 3: 1e-5}
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("version", [1, 2, 3])
+def test_fp32_smooth_flow_1000_steps(cuda, kernel, version):
+    """FP32 storage and arithmetic (compensated temperature numerator) vs the
+    FP64 oracle, on both kernels (the grid is short enough that the automatic
+    choice would take the plain one) and every equilibrium version."""
+    cfg = _cfg(160, 44, BCS["periodic"], "fp32", dt=1e-4, version=version)
     rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 40)
     p = oracle_params(cfg)
-    f0 = oeq.feq(rho, ux, uy, T)
+    f0 = oeq.feq(rho, ux, uy, T, version=version)
     with Simulation(cfg) as sim:
+        sim.set_kernel(KERNELS[kernel])
         sim.init_equilibrium(rho, ux, uy, T)
         sim.step(1000)
         r, a, b, t = sim.macros()
-    f = fdlb.run(f0, p, 1000)
-    ro, ao, bo, to = fdlb.macros(f)
+    ro, ao, bo, to = _oracle_run(("smooth", version), f0, p, 1000)
     assert np.abs(r / ro - 1).max() < 1e-5
     assert np.abs(t / to - 1).max() < 1e-5
     umax = max(np.abs(ao).max(), np.abs(bo).max())
-    assert np.abs(a - ao).max() < 1e-5 * umax and np.abs(b - bo).max() < 1e-5 * umax
+    tol = U_BOUND[version] * umax
+    assert np.abs(a - ao).max() < tol and np.abs(b - bo).max() < tol
 
 
 @pytest.mark.parametrize("bc", ["walls_x", "walls_y", "reflect_y", "inflow", "diffuse_x"])
@@ -155,16 +178,18 @@ def test_fp32_boundaries_300_steps(cuda, bc):
     assert np.abs(a - ao).max() < 1e-5 * umax and np.abs(b - bo).max() < 1e-5 * umax
 
 
-def test_fp32_across_shocks_l1(cuda):
-    """Richtmyer-Meshkov set-up (shock + interface) on 512 x 128, 200 steps."""
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_fp32_across_shocks_l1(cuda, kernel):
+    """Richtmyer-Meshkov set-up (shock + interface) on 512 x 128, 200 steps,
+    on both kernels."""
     cfg, (rho, ux, uy, T) = workloads.richtmyer_meshkov(nx=512, ny=128, dt=1e-5)
     p = oracle_params(cfg)
     with Simulation(cfg) as sim:
+        sim.set_kernel(KERNELS[kernel])
         sim.init_equilibrium(rho, ux, uy, T)
         sim.step(200)
         r, a, b, t = sim.macros()
-    f = fdlb.run(oeq.feq(rho, ux, uy, T), p, 200)
-    ro, ao, bo, to = fdlb.macros(f)
+    ro, ao, bo, to = _oracle_run("rm", oeq.feq(rho, ux, uy, T), p, 200)
     l1 = lambda x, y: np.abs(x - y).mean() / np.abs(y).mean()
     assert l1(r, ro) < 1e-4 and l1(t, to) < 1e-4
     assert np.abs(a - ao).mean() < 1e-4 * np.abs(ao).mean()
