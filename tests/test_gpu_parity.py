@@ -160,18 +160,20 @@ def test_fp32_smooth_flow_1000_steps(cuda, kernel, version):
 
 
 @pytest.mark.parametrize("bc", ["walls_x", "walls_y", "reflect_y", "inflow", "diffuse_x"])
-def test_fp32_boundaries_300_steps(cuda, bc):
-    """FP32 with NEE walls (filled in FP32 each step), reflecting and inflow
-    sides vs the FP64 oracle."""
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_fp32_boundaries_300_steps(cuda, bc, kernel):
+    """FP32 with NEE walls (filled in FP32 each step), reflecting, inflow and
+    diffuse sides vs the FP64 oracle, on both kernels."""
     cfg = _cfg(150, 37, BCS[bc], "fp32", dt=1e-4)
     rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 45)
     p = oracle_params(cfg)
     f0 = fdlb.prepare(oeq.feq(rho, ux, uy, T), p)
     with Simulation(cfg) as sim:
+        sim.set_kernel(KERNELS[kernel])
         sim.set_f(f0.astype(np.float32))
         sim.step(300)
         r, a, b, t = sim.macros()
-    ro, ao, bo, to = fdlb.macros(fdlb.run(f0.astype(np.float32).astype(np.float64), p, 300))
+    ro, ao, bo, to = _oracle_run(("bc", bc), f0.astype(np.float32).astype(np.float64), p, 300)
     assert np.abs(r / ro - 1).max() < 1e-5
     assert np.abs(t / to - 1).max() < 1e-5
     umax = max(np.abs(ao).max(), np.abs(bo).max())
