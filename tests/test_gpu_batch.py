@@ -27,6 +27,11 @@ def _instances(precision):
     cfg, fields = workloads.shock_bubble(nx=600, ny=30, precision=precision, radius=10.0)
     out.append((cfg, fields))
     out.append(workloads.slip_couette(nx=100, ny=5, precision=precision))
+    # per-instance models: equilibrium versions 3 and 2, and one instance
+    # without the energy-flux modification
+    out[2][0].eq_version = 3
+    out[3][0].modified = False
+    out[4][0].eq_version = 2
     return out
 
 
@@ -65,6 +70,8 @@ def test_batch_matches_instances_stepped_alone(cuda, precision):
 
 
 def test_batch_fp64_matches_oracle(cuda):
+    """Three instances with their own models (equilibrium version 3, no
+    modification, version 2) in one batch, each against the oracle."""
     insts = _instances("fp64")[2:5]
     sims = _sims(insts)
     with Batch(sims) as b:
@@ -74,8 +81,8 @@ def test_batch_fp64_matches_oracle(cuda):
         sides = tuple(fdlb.Side({"periodic": fdlb.PERIODIC, "outflow": fdlb.OUTFLOW,
                                  "wall": fdlb.WALL}[k], a, c, t) for k, a, c, t in cfg.bc)
         p = fdlb.Params(nx=cfg.nx, ny=cfg.ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt, s=np.asarray(cfg.s),
-                        sides=sides)
-        ref = fdlb.run(fdlb.prepare(oeq.feq(rho, ux, uy, T), p), p, 12)
+                        sides=sides, version=cfg.eq_version, modified=cfg.modified)
+        ref = fdlb.run(fdlb.prepare(oeq.feq(rho, ux, uy, T, version=cfg.eq_version), p), p, 12)
         assert _rel(s.get_f(), ref) < 1e-11
 
 
