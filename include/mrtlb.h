@@ -227,9 +227,13 @@ int mrtlb_launches_per_step(const mrtlb_ctx* ctx);
  * MRTLB_NOALLOC_MAX_NODES + 8 doubles (8 MiB), which every GPU that loads
  * this library holds until the process exits.  nx * ny above
  * MRTLB_NOALLOC_MAX_NODES is rejected with MRTLB_ERR_ARG before any device
- * work.  The first call on each device resolves the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The call allocates nothing.  All calls on a
+ * work.  The first call on each device, and the first in each new CUDA
+ * context of that device (e.g. after cudaDeviceReset), resolves the array's
+ * device address (cudaGetSymbolAddress) and the SM count with that device
+ * current; make that first call before any stream capture.  The call
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * A call that fails leaves no T_prev to compare with (the next call reports
+ * out[4] = 0).  All calls on a
  * device share the array (accumulators are cleared at each call, T_prev is
  * kept): calls that overlap on the GPU race.  CUDA failures give
  * MRTLB_ERR_CUDA. */
@@ -311,10 +315,19 @@ int mrtlb_get_rates(const mrtlb_ctx* ctx, double* s);
  *   mrtlb_get_f returns it (device FP64 [16][ny][nx], or NULL); recomputes
  *   each segment whose states are not held from its checkpoint (the context
  *   keeps f^K) and runs the adjoint steps back to f^0.  It may be called
- *   again with another seed after the same forward pass.  Outputs: dL_ds[16] (host;
+ *   again with another seed after the same forward pass.  It returns
+ *   MRTLB_ERR_STATE, computing nothing, when the context changed after the
+ *   forward pass (mrtlb_step, mrtlb_set_f, mrtlb_init_equilibrium,
+ *   mrtlb_bind, mrtlb_load, mrtlb_set_rates or a batched step), since its
+ *   gradients would then mix two runs.  Outputs: dL_ds[16] (host;
  *   entries 5..16 of the paper's s, 0-based 4..15, accumulated in FP64;
  *   0..3 are zero since those rates have no effect) and dL/df^0 (device FP64
  *   [16][ny][nx], or NULL).  Synchronises.
+ * mrtlb_adjoint_pass(ctx): the id (1, 2, ... per context) of the forward
+ *   pass that a backward pass would differentiate now, or 0 when there is
+ *   none (no forward pass yet, one that failed, or a context changed since);
+ *   a caller that holds several forward passes (e.g. an autograd graph)
+ *   compares it with the id it recorded after its own forward pass.
  * mrtlb_equilibrium_adjoint: for a state initialised by
  *   mrtlb_init_equilibrium from (rho, u_x, u_y, T) (device FP64 [ny][nx]),
  *   maps dL/df (device FP64 [16][ny][nx]) to dL/d(rho, u_x, u_y, T)
@@ -323,6 +336,7 @@ int mrtlb_adjoint_forward(mrtlb_ctx* ctx, long K);
 int mrtlb_adjoint_set_interval(mrtlb_ctx* ctx, long S);
 int mrtlb_adjoint_backward(mrtlb_ctx* ctx, const double* dL_dmacros, const double* dL_dfK,
                            double dL_ds[16], double* dL_df0);
+long long mrtlb_adjoint_pass(const mrtlb_ctx* ctx);
 int mrtlb_adjoint_release(mrtlb_ctx* ctx);
 int mrtlb_equilibrium_adjoint(mrtlb_ctx* ctx, const double* dL_df, const double* rho,
                               const double* ux, const double* uy, const double* T,

@@ -385,6 +385,9 @@ struct mrtlb_adjoint_state {
   std::vector<CUtensorMap> fmap;
   CUtensorMap lmap[2];
   int m_nstrips = 0, m_nseg = 0, m_seglen = 0;
+  // the context's generation when the forward pass ended, and the pass's id
+  unsigned long long gen = 0;
+  long long pass = 0;
 };
 
 namespace {
@@ -650,6 +653,7 @@ int forward_impl(mrtlb_ctx* c, long K) {
   const size_t sb = c->state_bytes;
   cudaStream_t st = c->stream;
   mrtlb_adjoint_state* old = c->adj;
+  if (old) old->pass = 0;  // until this pass completes, no backward pass is possible
   // segment length: every state when K + 2 states fit in half the free
   // memory (the buffers of a previous forward pass count as free)
   long S = c->adj_interval;
@@ -688,9 +692,12 @@ int forward_impl(mrtlb_ctx* c, long K) {
     run_segment<R>(c, a, len, coef_of<R>(c), st, (R*)c->f[c->cur ^ 1]);
     c->cur ^= 1;
     c->steps += len;
+    ++c->gen;
   }
   a->held = a->nseg - 1;
   ACK(cudaGetLastError(), "adjoint forward");
+  a->gen = c->gen;
+  a->pass = ++c->adj_passes;
   return MRTLB_OK;
 }
 
@@ -715,11 +722,20 @@ extern "C" int mrtlb_adjoint_backward(mrtlb_ctx* c, const double* dL_dmacros, co
                                       double dL_ds[16], double* dL_df0) {
   TraceRange trace_("mrtlb_adjoint_backward");
   if (!c) return MRTLB_ERR_ARG;
-  if (!c->adj) return afail(c, MRTLB_ERR_STATE, "call mrtlb_adjoint_forward first");
+  if (!c->adj || c->adj->pass == 0) return afail(c, MRTLB_ERR_STATE, "call mrtlb_adjoint_forward first");
+  if (c->adj->gen != c->gen)
+    return afail(c, MRTLB_ERR_STATE,
+                 "the state or the rates changed since mrtlb_adjoint_forward (a step, set_f, init_equilibrium, "
+                 "bind, load, set_rates or a batched step): run the forward pass again");
   if (!dL_dmacros && !dL_dfK) return afail(c, MRTLB_ERR_ARG, "a seed (dL/dmacros or dL/df^K) is required");
   const int rc = (c->prec == MRTLB_FP64) ? backward_impl<double>(c, dL_dmacros, dL_dfK, dL_ds, dL_df0)
                                          : backward_impl<float>(c, dL_dmacros, dL_dfK, dL_ds, dL_df0);
   return rc;
+}
+
+extern "C" long long mrtlb_adjoint_pass(const mrtlb_ctx* c) {
+  if (!c || !c->adj || c->adj->gen != c->gen) return 0;
+  return c->adj->pass;
 }
 
 extern "C" int mrtlb_adjoint_release(mrtlb_ctx* c) {

@@ -354,6 +354,10 @@ int set_tiles(mrtlb_batch* b, int bx, int seglen) {
   b->bx = bx;
   b->seglen = seglen;
   drop_graphs(b);
+  // both tile counters start at zero whatever parity the next step has (the
+  // tuner's trial launches, and any launches of the old tiles, leave the
+  // counter of their last parity at the old tile count)
+  if (b->claim) BCK(cudaMemsetAsync(b->claim, 0, 2 * sizeof(int), b->stream), "clear tile counters");
   return MRTLB_OK;
 }
 
@@ -409,6 +413,7 @@ int run_steps(mrtlb_batch* b, long nsteps) {
   for (mrtlb_ctx* c : b->ctx) {
     c->cur = b->cur;
     c->steps += nsteps;
+    if (nsteps > 0) ++c->gen;
   }
   return MRTLB_OK;
 }

@@ -144,6 +144,6 @@ extern "C" int mrtlb_load(mrtlb_ctx* c, const char* path) {
   if (!why.empty()) return ck_fail(c, MRTLB_ERR_ARG, why + ": " + path);
   const int rc = mrtlb_set_f(c, data.data(), 0);
   if (rc) return rc;
-  c->steps = (long)steps;
+  c->steps = (long)steps;  // (mrtlb_set_f advanced the generation)
   return MRTLB_OK;
 }

@@ -37,6 +37,11 @@ struct mrtlb_ctx {
   void* f[2] = {nullptr, nullptr};
   int cur = 0;
   long steps = 0;
+  // bumped by every call that changes the state or the rates (a step, set_f,
+  // init_equilibrium, bind, load, set_rates, a batched step); the adjoint's
+  // backward pass refuses a context changed since its forward pass
+  unsigned long long gen = 0;
+  long long adj_passes = 0;  // forward passes of the adjoint so far
   cudaStream_t stream = nullptr;
   int kernel = MRTLB_KERNEL_AUTO;
   // library-owned scratch

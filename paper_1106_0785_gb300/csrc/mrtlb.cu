@@ -388,6 +388,7 @@ extern "C" int mrtlb_bind(mrtlb_ctx* c, void* f_a, void* f_b, size_t bytes) {
   c->f[0] = f_a;
   c->f[1] = f_b;
   c->cur = 0;
+  ++c->gen;
   c->steps = 0;
   c->have_prev = 0;
   int rc = ensure_scratch(c);
@@ -438,6 +439,7 @@ extern "C" int mrtlb_init_equilibrium(mrtlb_ctx* c, const double* rho, const dou
     r = s; a = s + n; b = s + 2 * n; t = s + 3 * n;
   }
   c->cur = 0;
+  ++c->gen;
   CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");  // a new run
   if (c->prec == MRTLB_FP64) launch_init_eq<double>(r, a, b, t, (double*)c->f[0], c->L, c->c64, c->stream);
   else launch_init_eq<float>(r, a, b, t, (float*)c->f[0], c->L, c->c64, c->stream);
@@ -516,6 +518,7 @@ static int enqueue_steps(mrtlb_ctx* c, long nsteps) {
     c->cur ^= 1;
   }
   c->steps += nsteps;
+  if (nsteps > 0) ++c->gen;
   return check_launch(c, "step");
 }
 
@@ -641,6 +644,7 @@ extern "C" int mrtlb_set_f(mrtlb_ctx* c, const void* f, int on_device) {
     src = c->staging;
   }
   c->cur = 0;
+  ++c->gen;
   CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), "clear error word");  // a new run
   if (c->prec == MRTLB_FP64) launch_pack<double>((const double*)src, (double*)c->f[0], c->L, c->stream);
   else launch_pack<float>((const float*)src, (float*)c->f[0], c->L, c->stream);
@@ -665,6 +669,7 @@ extern "C" int mrtlb_set_rates(mrtlb_ctx* c, const double* s) {
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
   }
   for (int q = 0; q < 16; ++q) c->s[q] = s[q];
+  ++c->gen;
   drop_graphs(c);  // captured launches hold the old coefficients
   return build_coefficients(c);
 }

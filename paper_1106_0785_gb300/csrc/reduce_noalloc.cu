@@ -9,6 +9,7 @@
 // temperatures for the residual) lives in one file-scope static device
 // array, so every GPU that loads this library holds that array until the
 // process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,8 +26,46 @@ static __device__ __align__(256) double g_noalloc_scratch[kAcc + MRTLB_NOALLOC_M
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-double* g_scratch[kMaxDevices] = {nullptr};  // device address of g_noalloc_scratch
-int g_prev_nx[kMaxDevices] = {0}, g_prev_ny[kMaxDevices] = {0};
+// Per device: the CUDA context the entry was set up in, the device address
+// of g_noalloc_scratch in that context, the device's SM count, and the grid
+// shape of the last call that completed (its temperatures are in T_prev).
+// A context created anew (e.g. after cudaDeviceReset) may load the module
+// at another address, so the entry is set up again when the context's id
+// changes.
+struct DeviceEntry {
+  unsigned long long ctx_id = 0;
+  double* scratch = nullptr;
+  int sms = 0;
+  int prev_nx = 0, prev_ny = 0;
+};
+DeviceEntry g_dev[kMaxDevices];
+
+// The driver's id of the calling thread's current context (0 if none):
+// cuCtxGetCurrent and cuCtxGetId through the runtime's driver entry points,
+// so the library needs no link against the driver library.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)p;
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 template <typename R>
 __global__ void reduce_dense_kernel(const R* __restrict__ f, int nx, int ny, double* scratch,
@@ -77,35 +116,42 @@ extern "C" int mrtlb_reduce_noalloc(const void* f, int nx, int ny, int precision
   if ((long long)nx * ny > MRTLB_NOALLOC_MAX_NODES) return MRTLB_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MRTLB_ERR_CUDA;
-  double* scratch = nullptr;
-  int have_prev = 0;
-  {
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch[dev]) {
-      // once per device, with that device current: the host-side name of a
-      // __device__ array is not a device address, so resolve it here
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MRTLB_ERR_CUDA;
-      g_scratch[dev] = (double*)p;
-    }
-    scratch = g_scratch[dev];
-    have_prev = (g_prev_nx[dev] == nx && g_prev_ny[dev] == ny) ? 1 : 0;
-    g_prev_nx[dev] = nx;
-    g_prev_ny[dev] = ny;
+  const unsigned long long ctx_id = current_context_id();  // 0 before the runtime's first call
+  std::lock_guard<std::mutex> lock(g_mutex);  // calls share the array (and T_prev) anyway
+  DeviceEntry& d = g_dev[dev];
+  if (!d.scratch || ctx_id == 0 || d.ctx_id != ctx_id) {
+    // set-up, with the device current: the host-side name of a __device__
+    // array is not a device address, so resolve it in this context
+    d = DeviceEntry();
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MRTLB_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      return MRTLB_ERR_CUDA;
+    d.scratch = (double*)p;
+    d.sms = sms;
+    d.ctx_id = current_context_id();  // the context the runtime has made current by now
   }
+  double* scratch = d.scratch;
+  const int have_prev = (d.prev_nx == nx && d.prev_ny == ny) ? 1 : 0;
+  // from here until the launch completes T_prev is being rewritten: a failed
+  // call leaves no shape to compare against
+  d.prev_nx = d.prev_ny = 0;
   cudaStream_t st = (cudaStream_t)stream;
   // the array keeps the last call's contents: clear the accumulators
   if (cudaMemsetAsync(scratch, 0, kAcc * sizeof(double), st) != cudaSuccess) return MRTLB_ERR_CUDA;
   const long long n = (long long)nx * ny;
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 8LL * d.sms) blocks = 8LL * d.sms;  // 8 blocks of 256 threads per SM, grid-stride beyond
   if (precision == MRTLB_FP64)
-    reduce_dense_kernel<double><<<blocks, 256, 0, st>>>((const double*)f, nx, ny, scratch, have_prev);
+    reduce_dense_kernel<double><<<(int)blocks, 256, 0, st>>>((const double*)f, nx, ny, scratch, have_prev);
   else
-    reduce_dense_kernel<float><<<blocks, 256, 0, st>>>((const float*)f, nx, ny, scratch, have_prev);
+    reduce_dense_kernel<float><<<(int)blocks, 256, 0, st>>>((const float*)f, nx, ny, scratch, have_prev);
   if (cudaGetLastError() != cudaSuccess) return MRTLB_ERR_CUDA;
   if (cudaMemcpyAsync(out, scratch, 5 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return MRTLB_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return MRTLB_ERR_CUDA;
+  d.prev_nx = nx;
+  d.prev_ny = ny;
   return MRTLB_OK;
 }

@@ -53,7 +53,7 @@ EXPORTS = (
     "mrtlb_batch_get_tiles", "mrtlb_batch_set_graph_steps", "mrtlb_batch_tune", "mrtlb_batch_nodes",
     "mrtlb_batch_last_error", "mrtlb_batch_destroy",
     "mrtlb_set_rates", "mrtlb_get_rates", "mrtlb_selftest_wait", "mrtlb_adjoint_forward", "mrtlb_adjoint_set_interval", "mrtlb_adjoint_backward",
-    "mrtlb_adjoint_release", "mrtlb_equilibrium_adjoint", "mrtlb_measure_peak",
+    "mrtlb_adjoint_pass", "mrtlb_adjoint_release", "mrtlb_equilibrium_adjoint", "mrtlb_measure_peak",
     "mrtlb_save", "mrtlb_load",
 )
 
@@ -144,6 +144,8 @@ def load(path=LIB_PATH):
     lib.mrtlb_selftest_wait.argtypes = [P]
     lib.mrtlb_adjoint_set_interval.argtypes = [P, ctypes.c_long]
     lib.mrtlb_adjoint_backward.argtypes = [P, P, P, D, P]
+    lib.mrtlb_adjoint_pass.argtypes = [P]
+    lib.mrtlb_adjoint_pass.restype = ctypes.c_longlong
     lib.mrtlb_adjoint_release.argtypes = [P]
     lib.mrtlb_equilibrium_adjoint.argtypes = [P] + [P] * 9
     lib.mrtlb_measure_peak.argtypes = [ctypes.c_int, D]
@@ -375,6 +377,11 @@ def mrtlb_adjoint_backward(ctx, dL_dmacros=None, dL_dfK=None, dL_df0=None):
                                          ds.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                          _ptr(dL_df0)), ctx)
     return ds
+
+
+def mrtlb_adjoint_pass(ctx):
+    """Id of the forward pass a backward pass would differentiate now (0: none)."""
+    return int(load().mrtlb_adjoint_pass(ctx))
 
 
 def mrtlb_adjoint_release(ctx):

@@ -112,6 +112,10 @@ class Simulation:
             M.mrtlb_adjoint_set_interval(self.ctx, interval)
         M.mrtlb_adjoint_forward(self.ctx, K)
 
+    def adjoint_pass(self):
+        """Id of the forward pass adjoint_backward would differentiate (0: none)."""
+        return M.mrtlb_adjoint_pass(self.ctx)
+
     def adjoint_backward(self, dL_dmacros=None, dL_dfK=None, want_df0=True):
         """Seeds: device FP64 [4][ny][nx] (rho, ux, uy, T) and/or [16][ny][nx].
         Returns (dL/ds numpy[16], dL/df0 device FP64 [16][ny][nx] or None)."""

@@ -239,3 +239,58 @@ def test_repeated_passes_reuse_the_adjoint_state(cuda, kernel):
     assert np.allclose(d1, d2, rtol=1e-12, atol=0)
     assert np.array_equal(l3.cpu().numpy(), l4.cpu().numpy())
     assert np.allclose(d3, d4, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("change", ["step", "set_f", "set_rates", "init_equilibrium", "forward_again"])
+def test_backward_refuses_a_changed_context(cuda, change):
+    """A backward pass differentiates the forward pass it follows: any call
+    that changed the state or the rates in between makes it refuse
+    (MRTLB_ERR_STATE) rather than mix two runs; an unchanged context still
+    gives the same gradients."""
+    import torch
+    cfg = _cfg(40, 12, BCS["periodic"])
+    f0 = _state(cfg, 50)
+    w = torch.from_numpy(workloads.noise((16, cfg.ny, cfg.nx), 51)).to(cuda)
+    with Simulation(cfg) as sim:
+        sim.set_f(f0)
+        sim.adjoint_forward(3)
+        p1 = sim.adjoint_pass()
+        assert p1 > 0
+        ds1, _ = sim.adjoint_backward(dL_dfK=w)
+        rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 52)
+        if change == "step":
+            sim.step(1)
+        elif change == "set_f":
+            sim.set_f(f0)
+        elif change == "set_rates":
+            sim.set_rates(np.asarray(cfg.s))
+        elif change == "init_equilibrium":
+            sim.init_equilibrium(rho, ux, uy, T)
+        else:
+            sim.set_f(f0)
+            sim.adjoint_forward(3)
+            assert sim.adjoint_pass() == p1 + 1
+            ds2, _ = sim.adjoint_backward(dL_dfK=w)
+            assert np.allclose(ds2, ds1, rtol=1e-12, atol=0)
+            return
+        assert sim.adjoint_pass() == 0
+        with pytest.raises(M.MrtlbError) as e:
+            sim.adjoint_backward(dL_dfK=w)
+        assert e.value.code == M.MRTLB_ERR_STATE
+
+
+def test_autograd_refuses_an_overwritten_run(cuda):
+    """Two runs on one Simulation before backward: the first one's backward
+    raises (its checkpoints are gone), the second one's works."""
+    import torch
+    from paper_1106_0785_gb300 import autograd
+    cfg = _cfg(40, 12, BCS["periodic"])
+    rho, ux, uy, T = (torch.from_numpy(a).to(cuda) for a in workloads.smooth_fields(cfg.nx, cfg.ny, 53))
+    s = torch.tensor(cfg.s, dtype=torch.float64, requires_grad=True)
+    with Simulation(cfg) as sim:
+        out1 = autograd.run(sim, rho, ux, uy, T, s, 2)
+        out2 = autograd.run(sim, rho, ux, uy, T, s, 3)
+        out2[3].sum().backward(retain_graph=True)
+        assert torch.isfinite(s.grad).all()
+        with pytest.raises(RuntimeError, match="run or changed after this forward pass"):
+            out1[3].sum().backward()
