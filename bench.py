@@ -53,6 +53,7 @@ BYTES_PER_LUP_FP32 = 128
 STEP_FLOPS_PER_LUP = {"fp32": 539, "fp64": 521}
 CROP = (1600, 0, 512, 128)      # x0, y0, nx, ny of the CPU-baseline crop
 REF_CROP = (1900, 0, 128, 64)   # per-step sample of the reference arm
+PARITY_STEPS = 1000             # the CUDA path against the oracle on CROP after at least this many steps
 
 
 def parse():
@@ -69,6 +70,8 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=64)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--cpu-cores", type=int, default=0, help="oracle processes (0: one per host core)")
+    ap.add_argument("--ref-cores", type=int, default=0, help="reference-arm processes (0: one per host core)")
     return ap.parse_args()
 
 
@@ -223,16 +226,56 @@ def _crop_problem(crop):
     x0, y0, nx, ny = crop
     sl = (slice(y0, y0 + ny), slice(x0, x0 + nx))
     p = fdlb.Params(nx=nx, ny=ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt, s=np.asarray(cfg.s),
-                    sides=(fdlb.Side(fdlb.OUTFLOW), fdlb.Side(fdlb.OUTFLOW), fdlb.Side(), fdlb.Side()))
+                    sides=tuple(fdlb.Side(side[0], *side[1:]) for side in cfg.bc))
     return p, oeq.feq(rho[sl], ux[sl], uy[sl], T[sl])
 
 
-def cpu_baseline_worker(seconds, out=None):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def host_cores():
+    """Cores this process may run on (the affinity mask, else the count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _until(t_start):
+    while True:
+        d = t_start - time.time()
+        if d <= 0:
+            return
+        time.sleep(min(d, 0.05))
+
+
+def cpu_baseline_worker(seconds, out=None, t_start=0.0, min_steps=0):
+    """One thread: the oracle on the crop for about `seconds`, from t_start
+    (wall clock) so that the workers of one measurement run together.  With
+    `out`, the run then goes on (untimed) to at least min_steps steps and
+    saves the first and last states for the parity check."""
     import numpy as np
 
     from oracle import fdlb
     p, f0 = _crop_problem(CROP)
     f = fdlb.step(f0, p)  # warm-up (counted: the result is compared step for step)
+    _until(t_start)
     n, t0 = 1, time.perf_counter()
     while True:
         f = fdlb.step(f, p)
@@ -240,40 +283,68 @@ def cpu_baseline_worker(seconds, out=None):
         el = time.perf_counter() - t0
         if (el >= seconds and n >= 3) or n >= 100000:
             break
+    timed = n - 1
     if out:
+        while n < min_steps:
+            f = fdlb.step(f, p)
+            n += 1
         np.savez(out, f0=f0, fn=f)
-    print(json.dumps({"steps": n, "timed_steps": n - 1, "seconds": el, "nodes": p.nx * p.ny}))
+    print(json.dumps({"steps": n, "timed_steps": timed, "seconds": el, "nodes": p.nx * p.ny}))
 
 
-def cpu_baseline(seconds, dev=None):
-    """The oracle's rate on the crop (one thread, in a subprocess), and, when
-    a device is given, the CUDA path's error against the oracle's result on
-    that same crop after the same number of steps (FP32, the bench's
-    precision): returns (cpu_baseline, oracle_parity)."""
+def _run_workers(codes, timeout):
+    """Run one single-threaded Python worker per code string at once (fresh
+    processes: no state of this process, GPU or otherwise, is inherited);
+    returns their last stdout lines parsed as JSON, or raises."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = [subprocess.Popen([sys.executable, "-c", c], cwd=ROOT, env=env, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for c in codes]
+    outs = []
+    for pr in procs:
+        so, se = pr.communicate(timeout=timeout)
+        if pr.returncode != 0:
+            raise RuntimeError(se[-300:])
+        outs.append(json.loads(so.strip().splitlines()[-1]))
+    return outs
+
+
+def cpu_baseline(seconds, dev=None, cores=None):
+    """The oracle's rate on the crop on every host core: one independent
+    single-threaded process per core, started together; and, when a device
+    is given, the CUDA path's error against the oracle's result on that crop
+    after the same number of steps (FP32, the bench's precision): returns
+    (cpu_baseline, oracle_parity)."""
     import tempfile
 
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    n = cores or host_cores()
     with tempfile.TemporaryDirectory() as tmp:
         out = os.path.join(tmp, "oracle_crop.npz")
-        code = "import bench; bench.cpu_baseline_worker(%r, %r)" % (seconds, out)
-        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
-                           text=True, timeout=600)
-        if r.returncode != 0:
-            return {"error": r.stderr[-300:]}, None
-        d = json.loads(r.stdout.strip().splitlines()[-1])
-        parity = crop_parity(out, d["steps"], dev) if dev is not None else None
-    mlups = d["nodes"] * d["timed_steps"] / d["seconds"] / 1e6
+        t_start = time.time() + 3.0 + 0.1 * n  # after every worker has imported and warmed up
+        keep = dev is not None  # the first worker also serves the parity check
+        codes = ["import bench; bench.cpu_baseline_worker(%r, %r, %r, %d)"
+                 % (seconds, out if (i == 0 and keep) else None, t_start, PARITY_STEPS if (i == 0 and keep) else 0)
+                 for i in range(n)]
+        try:
+            ds = _run_workers(codes, timeout=600 + 10 * n)
+        except (RuntimeError, subprocess.SubprocessError) as e:
+            return {"error": str(e)[-300:]}, None
+        parity = crop_parity(out, ds[0]["steps"], dev) if dev is not None else None
+    per = [d["nodes"] * d["timed_steps"] / d["seconds"] / 1e6 for d in ds]
     x0, y0, nx, ny = CROP
-    base = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "FP64 numpy oracle, %d steps of a %dx%d crop (x %d-%d, y %d-%d) of the "
-                      "Richtmyer-Meshkov 4096x1024 initial state, one thread, %.1f s"
-                      % (d["timed_steps"], nx, ny, x0, x0 + nx - 1, y0, y0 + ny - 1, d["seconds"])}
+    base = {"value": sum(per), "unit": "MLUPS", "cores": n, "kind": "oracle",
+            "per_core_mlups": sum(per) / n, "cpu_model": cpu_model(),
+            "sample": "FP64 numpy oracle, %d single-threaded processes at once (one per host core), each "
+                      "%d-%d timed steps of a %dx%d crop (x %d-%d, y %d-%d) of the Richtmyer-Meshkov 4096x1024 "
+                      "initial state for about %.0f s; value = the sum of their rates"
+                      % (n, min(d["timed_steps"] for d in ds), max(d["timed_steps"] for d in ds), nx, ny,
+                         x0, x0 + nx - 1, y0, y0 + ny - 1, seconds)}
     return base, parity
 
 
 def crop_parity(path, steps, dev):
     """The FP32 CUDA path (the row-march kernel the bench times) on the
-    oracle's crop problem (outflow in x, periodic in y), from the same
+    oracle's crop problem (the workload's sides: the post-shock inflow on
+    the left, outflow on the right, periodic in y), from the same
     initial state for the same steps: the largest relative error in rho and
     T and in u relative to max |u|."""
     import numpy as np
@@ -286,8 +357,7 @@ def crop_parity(path, steps, dev):
     z = np.load(path)
     cfg, _ = workloads.richtmyer_meshkov(nx=NX, ny=NY)
     x0, y0, nx, ny = CROP
-    crop = M.Config(nx=nx, ny=ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt, s=cfg.s,
-                    bc=(("outflow", 0, 0, 1),) * 2 + (("periodic", 0, 0, 1),) * 2,
+    crop = M.Config(nx=nx, ny=ny, dx=cfg.dx, dy=cfg.dy, dt=cfg.dt, s=cfg.s, bc=cfg.bc,
                     eq_version=cfg.eq_version, modified=cfg.modified, precision="fp32")
     with Simulation(crop, device=dev) as sim:
         sim.set_kernel(M.MRTLB_KERNEL_TILED)  # the kernel the bench times (the crop is short enough
@@ -306,30 +376,47 @@ def crop_parity(path, steps, dev):
 # ---------------------------------------------------------------------------
 # reference arm: the oracle as it stands on the host cores
 # ---------------------------------------------------------------------------
-def run_reference(args, world, rank):
-    if rank != 0:
-        return
+def reference_worker(warmup, steps, t_start):
+    """One thread: `warmup` then `steps` oracle steps of the reference crop,
+    the timed steps from t_start (wall clock)."""
     from oracle import fdlb
     p, f = _crop_problem(REF_CROP)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         f = fdlb.step(f, p)
+    _until(t_start)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         f = fdlb.step(f, p)
-    el = time.perf_counter() - t0
-    mlups = p.nx * p.ny * args.steps / el / 1e6
+    print(json.dumps({"seconds": time.perf_counter() - t0, "nodes": p.nx * p.ny}))
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands on every host core: one single-threaded
+    process per core, each advancing its own copy of the crop, timed
+    together; a bench step is one time step of every copy."""
+    if rank != 0:
+        return
+    n = args.ref_cores or host_cores()
+    t_start = time.time() + 3.0 + 0.1 * n + 0.05 * args.warmup
+    ds = _run_workers(["import bench; bench.reference_worker(%d, %d, %r)" % (args.warmup, args.steps, t_start)
+                       for _ in range(n)], timeout=600 + 10 * n)
+    el = max(d["seconds"] for d in ds)
+    nodes = ds[0]["nodes"]
+    mlups = n * nodes * args.steps / el / 1e6
     x0, y0, nx, ny = REF_CROP
-    sample = ("FP64 numpy oracle, one time step of a %dx%d crop (x %d-%d, y %d-%d) of the "
-              "Richtmyer-Meshkov 4096x1024 initial state per bench step" % (nx, ny, x0, x0 + nx - 1, y0, y0 + ny - 1))
+    sample = ("FP64 numpy oracle, %d single-threaded processes at once (one per host core), each one time "
+              "step of its own %dx%d crop (x %d-%d, y %d-%d) of the Richtmyer-Meshkov 4096x1024 initial "
+              "state per bench step" % (n, nx, ny, x0, x0 + nx - 1, y0, y0 + ny - 1))
     line = {
         "impl": "reference", "metric": "MLUPS, FP32 forward step (Richtmyer-Meshkov 4096x1024)",
         "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "richtmyer_meshkov_4096x1024", "nx": NX, "ny": NY,
-                   "precision": "fp64 (the oracle)", "parallelism": "host cores, one thread",
+                   "precision": "fp64 (the oracle)", "parallelism": "host cores, %d processes" % n,
                    "sample": sample},
-        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": n, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -489,48 +576,62 @@ def run_mine(args, world, rank, local):
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"], line["oracle_parity"] = cpu_baseline(args.cpu_seconds, dev)
+        line["cpu_baseline"], line["oracle_parity"] = cpu_baseline(args.cpu_seconds, dev, args.cpu_cores or None)
     print(json.dumps(line), flush=True)
 
 
 def run_fwd_adj(args, world, dev, cfg, fields, nodes):
-    """K FP32 steps forward (states kept for the backward pass), then the
-    adjoint back to the initial state (seed: dL/dT = 1 on every node).
-    MLUPS = nodes * K / total time; algorithmic bytes 320 / node update
-    (forward 128 + adjoint: read f, read lambda, write lambda, 64 each).
-    The timed pass follows a warm-up pass of the same length, so it reuses
-    the stored-state buffers and plans, as every pass of a gradient loop
-    after the first does."""
+    """K FP32 steps forward, then the adjoint back to the initial state
+    (seed: dL/dT = 1 on every node), two ways: with sqrt(K) checkpointing
+    (segments of ceil(sqrt(K)) steps; every segment but the last is
+    recomputed from its checkpoint in the backward pass) and with every
+    state stored (no recomputation).  MLUPS = nodes * K / total time;
+    algorithmic bytes 320 / node update (forward 128 + adjoint: read f, read
+    lambda, write lambda, 64 each); the recomputed steps' traffic is extra,
+    not counted.  Each timed pass follows a warm-up pass of the same shape,
+    so it reuses the library's buffers and plans, as every pass of a
+    gradient loop after the first does."""
     import torch
 
     from paper_1106_0785_gb300.simulation import Simulation
 
     K = args.adjoint_steps
-    sim = Simulation(cfg, device=dev)
-    # the library keeps all K states when K + 2 fit in half the free memory,
-    # else a segment of ceil(sqrt(K)) states plus checkpoints
-    free, _ = torch.cuda.mem_get_info(dev)
-    seg = K if (K + 2) * sim.state_bytes <= free // 2 else int(math.ceil(math.sqrt(K)))
+    peak, _ = measured_peaks()
     seed = torch.zeros((4, cfg.ny, cfg.nx), dtype=torch.float64, device=dev)
     seed[3] = 1.0
-    sim.init_equilibrium(*fields)
-    sim.adjoint_forward(K)  # warm-up (allocations, graphs)
-    sim.adjoint_backward(dL_dmacros=seed, want_df0=False)
-    sim.init_equilibrium(*fields)
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    sim.adjoint_forward(K)
-    ds, _ = sim.adjoint_backward(dL_dmacros=seed, want_df0=False)
-    torch.cuda.synchronize(dev)
-    el = max_over_ranks(time.perf_counter() - t0, world, dev)
-    sim.close()
-    peak, _ = measured_peaks()
-    gbs = 320 * nodes * K / el / 1e9
-    return {"K": K, "segment_steps": seg, "recomputed_steps": K - seg if seg < K else 0,
-            "mlups": world * nodes * K / el / 1e6, "seconds": el,
-            "algorithmic_gbs": gbs, "frac_of_hbm": gbs / peak,
-            "dL_ds_visc": float(ds[4] + ds[5]), "dL_ds_cond": float(ds[6] + ds[7])}
+
+    def one(interval):
+        sim = Simulation(cfg, device=dev)
+        seg = max(1, min(interval, K))
+        nseg = (K + seg - 1) // seg
+        sim.init_equilibrium(*fields)
+        sim.adjoint_forward(K, interval=seg)  # warm-up (allocations, graphs)
+        sim.adjoint_backward(dL_dmacros=seed, want_df0=False)
+        sim.init_equilibrium(*fields)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sim.adjoint_forward(K, interval=seg)
+        ds, _ = sim.adjoint_backward(dL_dmacros=seed, want_df0=False)
+        torch.cuda.synchronize(dev)
+        el = max_over_ranks(time.perf_counter() - t0, world, dev)
+        sim.close()
+        gbs = 320 * nodes * K / el / 1e9
+        recomputed = (nseg - 1) * seg if nseg > 1 else 0
+        held = seg + (nseg if nseg > 1 else 0) + 2  # segment slots, checkpoints, two adjoint buffers
+        return {"segment_steps": seg, "segments": nseg, "recomputed_steps": recomputed,
+                "mlups": world * nodes * K / el / 1e6, "seconds": el,
+                "algorithmic_gbs": gbs, "frac_of_hbm": gbs / peak,
+                "state_memory_bytes": held * sim.state_bytes,
+                "recompute_bytes": recomputed * BYTES_PER_LUP_FP32 * nodes,
+                "dL_ds_visc": float(ds[4] + ds[5]), "dL_ds_cond": float(ds[6] + ds[7])}
+
+    ck = one(int(math.ceil(math.sqrt(K))))
+    stored = one(K)
+    out = {"K": K, "checkpointing": "sqrt(K)"}
+    out.update(ck)
+    out["stored_states"] = stored
+    return out
 
 
 def run_small(dev):
@@ -618,9 +719,6 @@ def run_batched(args, world, dev):
 def main():
     args = parse()
     if args.impl == "reference":
-        # one thread, as the line reports (before anything loads numpy's BLAS)
-        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-            os.environ[var] = "1"
         world, rank, _ = dist_init("gloo")
         run_reference(args, world, rank)
         return

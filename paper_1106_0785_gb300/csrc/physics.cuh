@@ -214,7 +214,7 @@ MRTLB_HD NodeMac<R> node_macros(const R g[16]) {
 }
 
 // One velocity's Lax-Wendroff update with the collision term,
-// f0 + sum_n k_qn (f_n - f0) - C, given the four neighbours' values.  The
+// f0 + (sum_n k_qn (f_n - f0) - C), given the four neighbours' values.  The
 // difference form keeps a uniform region exactly uniform (every f_n - f0
 // is an exact zero there); the fused form below (MRTLB_LW_WEIGHTS = 1) takes
 // fewer operations but makes the same rounding error at every node of a
@@ -239,15 +239,19 @@ MRTLB_HD R lw_update(const Coef<R>& c, int q, R f0, R Cq, R fE, R fW, R fN, R fS
     v = fma(c.lw[q][3], fS, v);
   }
 #else
-  R v = f0 - Cq;
+  // the increment is summed first and added to f0 once: each partial sum
+  // rounds at the increment's own (small) magnitude, and only the final
+  // addition at f0's, instead of all five (same operation count)
+  R d = -Cq;
   if (vx_of(q) != 0) {
-    v += c.lw[q][0] * (fE - f0);
-    v += c.lw[q][1] * (fW - f0);
+    d += c.lw[q][0] * (fE - f0);
+    d += c.lw[q][1] * (fW - f0);
   }
   if (vy_of(q) != 0) {
-    v += c.lw[q][2] * (fN - f0);
-    v += c.lw[q][3] * (fS - f0);
+    d += c.lw[q][2] * (fN - f0);
+    d += c.lw[q][3] * (fS - f0);
   }
+  const R v = f0 + d;
 #endif
   return v;
 }

@@ -55,3 +55,17 @@ def test_reference_arm_under_torchrun_two_ranks():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["cores"] >= 1
+
+
+def test_cpu_baseline_runs_one_oracle_process_per_core():
+    """The oracle baseline: independent single-threaded processes started
+    together; the value is the sum of their rates, the core count is the
+    number of processes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    base, parity = bench.cpu_baseline(0.5, None, 2)
+    assert parity is None and "error" not in base, base
+    assert base["cores"] == 2 and base["kind"] == "oracle" and base["value"] > 0
+    assert abs(base["per_core_mlups"] * 2 - base["value"]) < 1e-9 * base["value"]
+    assert "2 single-threaded processes" in base["sample"]
