@@ -161,3 +161,33 @@ def test_fig2_growth_under_this_reading(case):
         assert mrt > 1.0 + 1e-3
     else:                # the paper: MRT stable, SRT not; here MRT grows faster
         assert mrt > srt
+
+
+def test_rm_hot_states_unstable_at_diagonal_grid_modes():
+    """The Richtmyer-Meshkov grid (dx = dy = 1/4096, Fig. 7(b) rates): hot,
+    fast states like those behind the refracted shock are weakly unstable
+    under G at grid-scale diagonal modes (kx dx = ky dy), less so per step at
+    the smaller time step; the cold, slow states are not."""
+    s = np.full(16, 1e5)
+    s[:4] = 0.0
+    s[4:8] = 1e4
+    d = 1.0 / 4096
+    ks = np.linspace(0.0, np.pi, 25)
+
+    def growth(dt, state):
+        p = fdlb.Params(nx=8, ny=8, dx=d, dy=d, dt=dt, s=s)
+        best, arg = 0.0, None
+        for a in ks:
+            for b in ks:
+                g = np.abs(np.linalg.eigvals(amplification_matrix(p, *state, a / d, b / d))).max()
+                if g > best:
+                    best, arg = g, (a, b)
+        return best, arg
+
+    hot = (1.1, 1.27, 0.0, 2.7)
+    g1, (a1, b1) = growth(1e-5, hot)
+    g2, _ = growth(5e-6, hot)
+    assert g1 > 1.01 and 1.0 < g2 < g1
+    assert a1 > 0.5 and b1 > 0.5 and abs(a1 - b1) < 0.3  # a diagonal mode at grid scale
+    for cold in ((1.5, 0.3, 0.0, 1.0), (1.0, 0.0, 0.0, 0.3)):
+        assert growth(1e-5, cold)[0] < 1.0 + 1e-9
