@@ -14,12 +14,17 @@ Eq. 5):
 All functions broadcast over arrays of any shape and accept complex input
 (complex-step differentiation).
 
-Parity unpinned: the version-2 formulas.  The paper derives them from the
-requirement that the model reduce to an earlier single-relaxation-time model
-(Chen 1994), which is not part of the paper, so they are pinned only as the
-text states them; they still leave the conserved moments untouched and the
-collision conserving.  Versions 1 and 3 are pinned (version 3 against the
-discrete Maxwellian's moments).
+Parity unpinned: the values of the version-2 formulas.  The paper derives
+them from the requirement that the model reduce to an earlier
+single-relaxation-time model (Chen 1994), which is not part of the paper,
+so their values are pinned only as the text states them.  What the paper
+does fix about them is checked: they leave the conserved moments untouched
+and the collision conserving; they turn into each other under the lattice's
+90-degree rotation and reflections (a sign or swap slip in one of the two
+fails); and, as Sec. II states for every choice of f^12, f^15, f^16, the
+scheme's hydrodynamic modes agree with version 1's up to third order in k.
+Versions 1 and 3 are pinned (version 3 against the discrete Maxwellian's
+moments).
 """
 import numpy as np
 

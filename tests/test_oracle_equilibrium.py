@@ -99,3 +99,60 @@ def test_primitive_inverts_conserved():
     e = rho * (T + 0.5 * (ux * ux + uy * uy))
     u1, u2, T1 = eq.primitive(rho, rho * ux, rho * uy, e)
     assert np.allclose([u1, u2, T1], [ux, uy, T], rtol=1e-14)
+
+
+def _lattice_maps():
+    """The square's symmetries acting on the velocities: (matrix g,
+    permutation p with v[p[i]] = g v[i])."""
+    from oracle import d2v16
+    v = d2v16.velocities().astype(int)
+    out = []
+    for g in (np.array([[0, -1], [1, 0]]), np.array([[1, 0], [0, -1]]), np.array([[0, 1], [1, 0]])):
+        p = np.array([int(np.flatnonzero((v == g @ vi).all(axis=1))[0]) for vi in v])
+        out.append((g, p))
+    return out
+
+
+@pytest.mark.parametrize("version", [1, 2, 3])
+def test_equilibrium_is_covariant_under_the_lattice_symmetries(version):
+    """f^eq_i(g u) = f^eq_j(u) with v_i = g v_j, for the 90-degree rotation and
+    the reflections of the square lattice (Fig. 1).  The moments of rows 15 and
+    16 (v^2 times the third harmonics) must turn into each other under the
+    rotation, f^15(R u) = f^16(u) and f^16(R u) = -f^15(u): a sign or a swap
+    slipped into one of version 2's two formulas breaks this."""
+    rng = np.random.default_rng(31)
+    rho = rng.uniform(0.5, 2.0, 50)
+    ux, uy = rng.uniform(-0.6, 0.6, (2, 50))
+    T = rng.uniform(0.5, 2.0, 50)
+    f = eq.feq(rho, ux, uy, T, version)
+    for g, p in _lattice_maps():
+        gu = g @ np.stack([ux, uy])
+        fg = eq.feq(rho, gu[0], gu[1], T, version)
+        assert np.allclose(fg[p], f, rtol=1e-13, atol=1e-14)
+
+
+def test_versions_differ_beyond_navier_stokes_order():
+    """Sec. II: the choice of f^12, f^15, f^16 at equilibrium has no effect on
+    the macroscopic equations.  The four hydrodynamic eigenvalues of the
+    scheme's amplification matrix G(k) (Sec. III) at a moving, non-uniform-rate
+    state are the same for versions 1, 2 and 3 up to terms of third order in
+    k: their difference falls eightfold per halving of k, while the modes
+    themselves move away from 1 at first order."""
+    from oracle import fdlb
+    from oracle.stability import amplification_matrix
+    s = np.array([0, 0, 0, 0, 800, 800, 1200, 1200, 900, 1100, 1000, 950, 1050, 1000, 1000, 1000.0])
+    p = fdlb.Params(nx=8, ny=8, dx=1e-2, dy=1e-2, dt=1e-5, s=s)
+
+    def hydro(version, kd):
+        p.version = version
+        G = amplification_matrix(p, 1.0, 0.3, 0.1, 1.2, kd / p.dx * np.cos(0.3), kd / p.dx * np.sin(0.3))
+        ev = np.linalg.eigvals(G)
+        ev = ev[np.argsort(np.abs(ev - 1.0))][:4]
+        return ev[np.argsort(ev.imag)]
+
+    for other in (2, 3):
+        d = [np.abs(hydro(other, kd) - hydro(1, kd)).max() for kd in (0.04, 0.02, 0.01)]
+        assert d[0] < 1e-9
+        assert 6.0 < d[0] / d[1] < 10.0 and 6.0 < d[1] / d[2] < 10.0, d
+    move = [np.abs(hydro(1, kd) - 1.0).max() for kd in (0.02, 0.01)]
+    assert 1.8 < move[0] / move[1] < 2.2
