@@ -23,7 +23,8 @@ Printed JSON line (rank 0):
              fused multiply-add ceilings measured on the device
   small      microseconds per step of the latency-bound small configurations
              (Sod 400 x 4 FP64, Couette 4 x 200 FP64 and FP32)
-  cpu_baseline  the FP64 numpy oracle on a crop of the same input, one thread
+  cpu_baseline  the FP64 oracle (its plain-C step) on a crop of the same input,
+                one single-threaded process per host core
   oracle_parity the FP32 CUDA path on that crop after the same steps, against
                 the oracle's result (largest errors in rho, u, T)
 
@@ -266,29 +267,31 @@ def _until(t_start):
 
 
 def cpu_baseline_worker(seconds, out=None, t_start=0.0, min_steps=0):
-    """One thread: the oracle on the crop for about `seconds`, from t_start
-    (wall clock) so that the workers of one measurement run together.  With
-    `out`, the run then goes on (untimed) to at least min_steps steps and
-    saves the first and last states for the parity check."""
+    """One thread: the oracle's C step on the crop for about `seconds`, from
+    t_start (wall clock) so that the workers of one measurement run
+    together.  With `out`, the run then goes on (untimed) to at least
+    min_steps steps and saves the first and last states for the parity
+    check."""
     import numpy as np
 
-    from oracle import fdlb
+    from oracle import cfdlb
     p, f0 = _crop_problem(CROP)
-    f = fdlb.step(f0, p)  # warm-up (counted: the result is compared step for step)
+    r = cfdlb.Runner(f0, p)
+    r.run(1)  # warm-up (counted: the result is compared step for step)
     _until(t_start)
     n, t0 = 1, time.perf_counter()
     while True:
-        f = fdlb.step(f, p)
+        r.run(1)
         n += 1
         el = time.perf_counter() - t0
         if (el >= seconds and n >= 3) or n >= 100000:
             break
     timed = n - 1
     if out:
-        while n < min_steps:
-            f = fdlb.step(f, p)
-            n += 1
-        np.savez(out, f0=f0, fn=f)
+        if n < min_steps:
+            r.run(min_steps - n)
+            n = min_steps
+        np.savez(out, f0=f0, fn=r.f)
     print(json.dumps({"steps": n, "timed_steps": timed, "seconds": el, "nodes": p.nx * p.ny}))
 
 
@@ -316,6 +319,8 @@ def cpu_baseline(seconds, dev=None, cores=None):
     (cpu_baseline, oracle_parity)."""
     import tempfile
 
+    from oracle import cfdlb
+    cfdlb.build()  # once, before the workers start
     n = cores or host_cores()
     with tempfile.TemporaryDirectory() as tmp:
         out = os.path.join(tmp, "oracle_crop.npz")
@@ -333,7 +338,7 @@ def cpu_baseline(seconds, dev=None, cores=None):
     x0, y0, nx, ny = CROP
     base = {"value": sum(per), "unit": "MLUPS", "cores": n, "kind": "oracle",
             "per_core_mlups": sum(per) / n, "cpu_model": cpu_model(),
-            "sample": "FP64 numpy oracle, %d single-threaded processes at once (one per host core), each "
+            "sample": "FP64 oracle (its plain-C step), %d single-threaded processes at once (one per host core), each "
                       "%d-%d timed steps of a %dx%d crop (x %d-%d, y %d-%d) of the Richtmyer-Meshkov 4096x1024 "
                       "initial state for about %.0f s; value = the sum of their rates"
                       % (n, min(d["timed_steps"] for d in ds), max(d["timed_steps"] for d in ds), nx, ny,
@@ -377,16 +382,17 @@ def crop_parity(path, steps, dev):
 # reference arm: the oracle as it stands on the host cores
 # ---------------------------------------------------------------------------
 def reference_worker(warmup, steps, t_start):
-    """One thread: `warmup` then `steps` oracle steps of the reference crop,
-    the timed steps from t_start (wall clock)."""
-    from oracle import fdlb
+    """One thread: `warmup` then `steps` steps of the oracle's C step on the
+    reference crop, the timed steps from t_start (wall clock)."""
+    from oracle import cfdlb
     p, f = _crop_problem(REF_CROP)
+    r = cfdlb.Runner(f, p)
     for _ in range(warmup):
-        f = fdlb.step(f, p)
+        r.run(1)
     _until(t_start)
     t0 = time.perf_counter()
     for _ in range(steps):
-        f = fdlb.step(f, p)
+        r.run(1)
     print(json.dumps({"seconds": time.perf_counter() - t0, "nodes": p.nx * p.ny}))
 
 
@@ -396,6 +402,8 @@ def run_reference(args, world, rank):
     together; a bench step is one time step of every copy."""
     if rank != 0:
         return
+    from oracle import cfdlb
+    cfdlb.build()  # once, before the workers start
     n = args.ref_cores or host_cores()
     t_start = time.time() + 3.0 + 0.1 * n + 0.05 * args.warmup
     ds = _run_workers(["import bench; bench.reference_worker(%d, %d, %r)" % (args.warmup, args.steps, t_start)
@@ -404,7 +412,7 @@ def run_reference(args, world, rank):
     nodes = ds[0]["nodes"]
     mlups = n * nodes * args.steps / el / 1e6
     x0, y0, nx, ny = REF_CROP
-    sample = ("FP64 numpy oracle, %d single-threaded processes at once (one per host core), each one time "
+    sample = ("FP64 oracle (its plain-C step), %d single-threaded processes at once (one per host core), each one time "
               "step of its own %dx%d crop (x %d-%d, y %d-%d) of the Richtmyer-Meshkov 4096x1024 initial "
               "state per bench step" % (n, nx, ny, x0, x0 + nx - 1, y0, y0 + ny - 1))
     line = {

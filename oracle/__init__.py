@@ -18,11 +18,15 @@ fdlb         the time step: boundaries, macroscopic recovery, collision with
              amplification matrix G of Sec. III)
 riemann      exact Riemann solver and Rankine-Hugoniot states for gamma = 2
 couette      closed-form thermal Couette temperature profile (Sec. IV A)
+stability    the amplification matrix G(k) of Sec. III
+cfdlb        the same time step as plain C loops (fdlb_c.c, built with gcc
+             -O3) for the periodic, outflow and inflow sides, pinned against
+             fdlb step by step; the bench's CPU legs time it
 
 Every function works on numpy arrays of float64; the step also accepts
 complex128 so that a complex-step derivative (Squire & Trapp 1998) gives the
 exact tangent of the step.
 
-Parity unpinned: equilibrium version 2 (see ``equilibrium``); every other
-function is pinned by the tests in ``tests/test_oracle_*.py``.
+Parity unpinned: the values of equilibrium version 2 (see ``equilibrium``);
+every other function is pinned by the tests in ``tests/test_oracle_*.py``.
 """
