@@ -134,7 +134,7 @@ FIG2 = {
 FIG2_GROWTH = {"a": (1.0000, 1.0000), "b": (1.0042, 1.0000), "c": (1.045, 1.005), "d": (1.061, 1.014)}
 
 
-def _fig2_growth(case):
+def _fig2_growth(case, version=1):
     state, printed = FIG2[case]
     s = np.full(16, 1e5)
     s[:4] = 0.0
@@ -144,9 +144,18 @@ def _fig2_growth(case):
     srt[:4] = 0.0
     out = []
     for rates in (s, srt):
-        p = fdlb.Params(nx=8, ny=8, dx=1e-3, dy=1e-3, dt=1e-5, s=rates)
+        p = fdlb.Params(nx=8, ny=8, dx=1e-3, dy=1e-3, dt=1e-5, s=rates, version=version)
         out.append(_max_eig(p, state, 0))
     return out
+
+
+@pytest.mark.parametrize("case", ["b", "c", "d"])
+def test_fig2_versions_do_not_differ_much(case):
+    """Sec. III: the three versions of the new model show no large
+    differences in stability; here their largest growth agrees to 1e-3."""
+    g1 = _fig2_growth(case, 1)[0]
+    for v in (2, 3):
+        assert abs(_fig2_growth(case, v)[0] - g1) < 1e-3
 
 
 @pytest.mark.parametrize("case", list(FIG2))
