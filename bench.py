@@ -303,11 +303,17 @@ def _run_workers(codes, timeout):
     procs = [subprocess.Popen([sys.executable, "-c", c], cwd=ROOT, env=env, stdout=subprocess.PIPE,
                               stderr=subprocess.PIPE, text=True) for c in codes]
     outs = []
-    for pr in procs:
-        so, se = pr.communicate(timeout=timeout)
-        if pr.returncode != 0:
-            raise RuntimeError(se[-300:])
-        outs.append(json.loads(so.strip().splitlines()[-1]))
+    try:
+        for pr in procs:
+            so, se = pr.communicate(timeout=timeout)
+            if pr.returncode != 0:
+                raise RuntimeError(se[-300:])
+            outs.append(json.loads(so.strip().splitlines()[-1]))
+    finally:
+        for pr in procs:  # after a failure, stop the workers still running
+            if pr.poll() is None:
+                pr.kill()
+                pr.wait()
     return outs
 
 
