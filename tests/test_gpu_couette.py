@@ -121,6 +121,7 @@ def _steady_many(cases, resid=1e-9, window=4096, max_steps=3_000_000):
                     # least-squares bump of T - 1 against y (1 - y), relative to the closed form's
                     out[k] = 1.0 - float((T - 1.0) @ q / (q @ q)) / bump
     finally:
+        torch.cuda.synchronize()  # no stream still works on the buffers released below
         for sim in sims:
             sim.close()
     assert all(o is not None for o in out), (cases, out)
