@@ -14,6 +14,7 @@ import pytest
 from oracle import couette as ocouette
 from oracle import equilibrium as oeq
 from oracle import fdlb
+from paper_1106_0785_gb300 import mrtlb as M
 from paper_1106_0785_gb300 import workloads
 from paper_1106_0785_gb300.simulation import Simulation
 
@@ -46,7 +47,7 @@ def test_couette_rate_gradients(cuda):
     with Simulation(cfg) as sim:
         sim.set_rates(s0)
         sim.init_equilibrium(*fields)
-        sim.adjoint_forward(K)
+        sim.adjoint_forward(K, interval=71)  # sqrt(K) checkpoints: 71 segments of 71 steps, 70 recomputed
         T = sim.macros()[3]
         seed = np.zeros((4, cfg.ny, cfg.nx))
         seed[3] = 2.0 * (T - target)
@@ -101,6 +102,7 @@ def test_richtmyer_meshkov_interface_gradient(cuda):
     cfg = make("fp32")
     dx = cfg.dx
     with Simulation(cfg) as sim:
+        M.mrtlb_adjoint_set_interval(sim.ctx, 29)  # sqrt(K) checkpoints: 28 segments of 29 steps, 27 recomputed
         a = torch.tensor(a0, dtype=torch.float64, device=cuda, requires_grad=True)
         s = torch.tensor(cfg.s, dtype=torch.float64)
         rho0, ux0, uy0, T0 = rm_initial_fields(a, nx, ny, x_shock=0.3, device=cuda)
