@@ -315,7 +315,9 @@ int mrtlb_get_rates(const mrtlb_ctx* ctx, double* s);
  *   mrtlb_get_f returns it (device FP64 [16][ny][nx], or NULL); recomputes
  *   each segment whose states are not held from its checkpoint (the context
  *   keeps f^K) and runs the adjoint steps back to f^0.  It may be called
- *   again with another seed after the same forward pass.  It returns
+ *   again with another seed after the same forward pass.  dL_ds may be
+ *   NULL: the adjoint steps then skip the rate gradients' work (the
+ *   moments and equilibria only they need), and dL/df^0 is the same.  It returns
  *   MRTLB_ERR_STATE, computing nothing, when the context changed after the
  *   forward pass (mrtlb_step, mrtlb_set_f, mrtlb_init_equilibrium,
  *   mrtlb_bind, mrtlb_load, mrtlb_set_rates or a batched step), since its

@@ -39,10 +39,12 @@ class MRTLBRun(torch.autograd.Function):
                                "one run(sim, ...) at a time, or give each run its own Simulation")
         zeros = lambda: torch.zeros((sim.cfg.ny, sim.cfg.nx), dtype=torch.float64, device=sim.device)
         seed = torch.stack([g if g is not None else zeros() for g in (g_rho, g_ux, g_uy, g_T)])
-        ds, df0 = sim.adjoint_backward(dL_dmacros=seed)
+        want_ds = ctx.needs_input_grad[4]  # rate gradients only when the rates need them
+        ds, df0 = sim.adjoint_backward(dL_dmacros=seed, want_ds=want_ds)
         rho0, ux0, uy0, T0 = ctx.saved_tensors
         d_rho, d_ux, d_uy, d_T = sim.equilibrium_adjoint(df0, rho0, ux0, uy0, T0)
-        return d_rho, d_ux, d_uy, d_T, torch.as_tensor(ds, device=ctx.s_device), None, None
+        d_s = torch.as_tensor(ds, device=ctx.s_device) if want_ds else None
+        return d_rho, d_ux, d_uy, d_T, d_s, None, None
 
 
 def run(sim, rho0, ux0, uy0, T0, s, K):

@@ -82,7 +82,7 @@ __device__ __forceinline__ R gbar_at(const R* gb, const Layout& L, int i, int j)
 
 // Pass 2: lambda~(p) for one node p of [-1, nx] x [-1, ny] (corners
 // excluded); the rate gradients of an advanced node are added to G.
-template <typename R>
+template <typename R, bool RATES>
 __device__ __forceinline__ void adj_core_node(const R* __restrict__ ft, const R* __restrict__ lam,
                                               const R* __restrict__ Ux, const R* __restrict__ Uy,
                                               const R* __restrict__ gsh, const R* __restrict__ gst,
@@ -107,7 +107,7 @@ __device__ __forceinline__ void adj_core_node(const R* __restrict__ ft, const R*
     const long long aE = at + 1, aW = at - 1, aN = at + L.pitch, aS = at - L.pitch;
     const R shear = (Ux[aE] - Ux[aW]) * c.inv2dx - (Uy[aN] - Uy[aS]) * c.inv2dy;
     const R strain = (Uy[aE] - Uy[aW]) * c.inv2dx + (Ux[aN] - Ux[aS]) * c.inv2dy;
-    collision_T_node(a, g, lp, ux, uy, shear, strain, lt, G);
+    collision_T_node<R, RATES>(a, g, lp, ux, uy, shear, strain, lt, G);
   }
   // (a) neighbours' Lax-Wendroff weights on p
   const int nbi[4] = {i - 1, i + 1, i, i};  // r = p - e_x (uses kE), p + e_x (kW), p - e_y (kN), p + e_y (kS)
@@ -142,7 +142,7 @@ __device__ __forceinline__ void adj_core_node(const R* __restrict__ ft, const R*
 // Persistent over row tiles of 128 nodes (tile t: row -1 + t / tiles_x);
 // each thread sums the rate gradients of all its nodes before the warp
 // reduction.
-template <typename R>
+template <typename R, bool RATES>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MRTLB_ADJ_MINB : 2)
     adj_core_kernel(const R* __restrict__ ft, const R* __restrict__ lam, const R* __restrict__ Ux,
                     const R* __restrict__ Uy, const R* __restrict__ gsh, const R* __restrict__ gst,
@@ -154,9 +154,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? MRTLB_ADJ_MINB : 2)
     const int i = -1 + (t % tiles_x) * 128 + (int)threadIdx.x;
     const int j = -1 + t / tiles_x;
     if (i <= L.nx && !((i < 0 || i >= L.nx) && (j < 0 || j >= L.ny)))
-      adj_core_node(ft, lam, Ux, Uy, gsh, gst, out, L, a, i, j, G);
+      adj_core_node<R, RATES>(ft, lam, Ux, Uy, gsh, gst, out, L, a, i, j, G);
   }
-  flush_rate_gradients(G, gacc);
+  if constexpr (RATES) flush_rate_gradients(G, gacc);
 }
 
 // Adjoint march shapes: 128-column strips (FP32; 64 for FP64, same box
@@ -401,7 +401,7 @@ int core_resident_blocks() {
   int dev = 0, nsm = 1, per = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj_core_kernel<R>, 128, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj_core_kernel<R, true>, 128, 0);
   return std::max(1, nsm) * std::max(1, per);
 #endif
 }
@@ -446,36 +446,46 @@ AdjCoef<R> adj_coef(const mrtlb_ctx* c, const Coef<R>& k) {
 
 template <typename R>
 void launch_adj_march(const mrtlb_adjoint_state* a, const Layout& L, const CUtensorMap& fm, const CUtensorMap& lm,
-                      R* out, const AdjCoef<R>& ac, int* err, cudaStream_t st) {
+                      R* out, const AdjCoef<R>& ac, int* err, bool rates, cudaStream_t st) {
   constexpr int BX = AdjTile<R>::BX, NF = AdjTile<R>::NF, NL = AdjTile<R>::NL;
   using SM = AdjSmem<R, BX, NF, NL>;
   static const bool attr = [] {  // once per instantiation (thread-safe static initialisation)
-    return cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SM::bytes) == cudaSuccess &&
+           cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)SM::bytes) == cudaSuccess;
   }();
   (void)attr;
   dim3 grid(a->m_nstrips, a->m_nseg);
-  adj_march_kernel<R, BX, NF, NL><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
+  if (rates)
+    adj_march_kernel<R, BX, NF, NL, true><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
+  else
+    adj_march_kernel<R, BX, NF, NL, false><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
 }
 
 // one adjoint step: lambda[li] (dL/df^{n+1}) -> lambda[li ^ 1] (dL/df^n),
-// ft = B(f^n) in slot n
+// ft = B(f^n) in slot n; rates: also sum the rate gradients
 template <typename R>
-void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, long n, int li, const Coef<R>& k, cudaStream_t st) {
+void adjoint_step(mrtlb_ctx* c, mrtlb_adjoint_state* a, long n, int li, const Coef<R>& k, bool rates,
+                  cudaStream_t st) {
   const Layout& L = c->L;
   const AdjCoef<R> ac = adj_coef<R>(c, k);
   const R* ft = (const R*)((char*)a->seg + (size_t)n * c->state_bytes);
   const R* lam_in = (const R*)a->lam[li];
   R* lam_out = (R*)a->lam[li ^ 1];
   if (a->march) {
-    launch_adj_march<R>(a, L, a->fmap[n], a->lmap[li], lam_out, ac, c->err, st);
+    launch_adj_march<R>(a, L, a->fmap[n], a->lmap[li], lam_out, ac, c->err, rates, st);
   } else {
     dim3 g2((L.nx + 2 + 127) / 128, L.ny + 2);
     adj_prep_kernel<R><<<g2, 128, 0, st>>>(ft, lam_in, (R*)a->ux, (R*)a->uy, (R*)a->gsh, (R*)a->gst, L, ac);
     const int ntiles = (int)(g2.x * g2.y);
     const int grid = std::min(ntiles, a->core_blocks);
-    adj_core_kernel<R><<<grid, 128, 0, st>>>(ft, lam_in, (const R*)a->ux, (const R*)a->uy, (const R*)a->gsh,
-                                             (const R*)a->gst, lam_out, L, ac, a->gacc, (int)g2.x, ntiles);
+    if (rates)
+      adj_core_kernel<R, true><<<grid, 128, 0, st>>>(ft, lam_in, (const R*)a->ux, (const R*)a->uy, (const R*)a->gsh,
+                                                     (const R*)a->gst, lam_out, L, ac, a->gacc, (int)g2.x, ntiles);
+    else
+      adj_core_kernel<R, false><<<grid, 128, 0, st>>>(ft, lam_in, (const R*)a->ux, (const R*)a->uy, (const R*)a->gsh,
+                                                      (const R*)a->gst, lam_out, L, ac, a->gacc, (int)g2.x, ntiles);
   }
   const int perim = 2 * L.nx + 2 * L.ny;
   adj_ghosts_kernel<R><<<dim3((perim + 127) / 128, 16), 128, 0, st>>>(lam_out, L);
@@ -501,13 +511,15 @@ bool plan_adj_march(mrtlb_ctx* c, mrtlb_adjoint_state* a) {
     if (encode_row_maps(L, es, s0, s1, BX, &a->fmap[n]) != 0) return false;
   }
   if (encode_row_maps(L, es, a->lam[0], a->lam[1], BX, a->lmap) != 0) return false;
-  if (cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SM::bytes) != cudaSuccess ||
+      cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)SM::bytes) != cudaSuccess)
     return false;
   int dev = 0, nsm = 1, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj_march_kernel<R, BX, NF, NL>, BX, SM::bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj_march_kernel<R, BX, NF, NL, true>, BX, SM::bytes);
   if (per < 1) return false;
   const int rows = L.ny + 2;  // output rows -1 .. ny
   a->m_nstrips = (L.nx + 2 + SM::SX - 1) / SM::SX;
@@ -584,7 +596,7 @@ int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, 
       a->held = sgi;
     }
     for (long n = len - 1; n >= 0; --n) {
-      adjoint_step<R>(c, a, n, li, k, st);
+      adjoint_step<R>(c, a, n, li, k, dL_ds != nullptr, st);
       li ^= 1;
     }
   }

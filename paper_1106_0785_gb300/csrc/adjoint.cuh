@@ -255,8 +255,9 @@ __device__ __forceinline__ void gbar_node(const Coef<R>& c, const R lam[16], R P
 // velocity u(p) and the two strain combinations of the forward step:
 // lt = (1 - sum_n k_qn) lp_q - (dC/dg)^T lp  (Lax-Wendroff self weight and
 // collision transpose, the temperature linearised at T = (e - j.u/2)/rho),
-// and the rate gradients of the node added to G[4..15].
-template <typename R>
+// and the rate gradients of the node added to G[4..15] (RATES = false
+// skips them and the moments and equilibria only they need; lt is the same).
+template <typename R, bool RATES = true>
 __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[16], const R lp[16], R ux, R uy,
                                                  R shear, R strain, R lt[16], R G[16]) {
   const Coef<R>& c = a.c;
@@ -266,11 +267,13 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
   const R T = (e - R(0.5) * (jx * ux + jy * uy)) * ir;
 #pragma unroll
   for (int q = 0; q < 16; ++q) lt[q] = a.selfw[q] * lp[q];
-  Harm<R> h;
-  harmonics(g, h);
   R m[16], eq[16];
-  moments(h, m);
-  equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eq);
+  if constexpr (RATES) {
+    Harm<R> h;
+    harmonics(g, h);
+    moments(h, m);
+    equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eq);
+  }
   const R Pp = rho * T;
   R Cb[16], cb[16];
 #pragma unroll
@@ -307,6 +310,7 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
   for (int q = 0; q < 16; ++q) lt[q] += fb[q];
   // rate gradients over dt: d f1 / d s_k through dt s_k (m_k - eq_k) and
   // the modification factors dt (s7/s5 - 1), ... (dL/dC = -lambda)
+  if constexpr (!RATES) return;
 #pragma unroll
   for (int k = 4; k < 16; ++k) G[k] += cb[k] * (m[k] - eq[k]);
   if (c.modified) {

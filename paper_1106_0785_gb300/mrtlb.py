@@ -370,11 +370,13 @@ def mrtlb_adjoint_set_interval(ctx, S):
     _check(load().mrtlb_adjoint_set_interval(ctx, int(S)), ctx)
 
 
-def mrtlb_adjoint_backward(ctx, dL_dmacros=None, dL_dfK=None, dL_df0=None):
-    """Device FP64 seeds in, (dL/ds numpy[16]) out; dL_df0 (device FP64) filled if given."""
-    ds = np.zeros(16)
+def mrtlb_adjoint_backward(ctx, dL_dmacros=None, dL_dfK=None, dL_df0=None, want_ds=True):
+    """Device FP64 seeds in, (dL/ds numpy[16], or None without want_ds) out;
+    dL_df0 (device FP64) filled if given.  Without want_ds the adjoint steps
+    skip the rate gradients' work."""
+    ds = np.zeros(16) if want_ds else None
     _check(load().mrtlb_adjoint_backward(ctx, _ptr(dL_dmacros), _ptr(dL_dfK),
-                                         ds.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ds.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_ds else None,
                                          _ptr(dL_df0)), ctx)
     return ds
 

@@ -116,14 +116,15 @@ class Simulation:
         """Id of the forward pass adjoint_backward would differentiate (0: none)."""
         return M.mrtlb_adjoint_pass(self.ctx)
 
-    def adjoint_backward(self, dL_dmacros=None, dL_dfK=None, want_df0=True):
+    def adjoint_backward(self, dL_dmacros=None, dL_dfK=None, want_df0=True, want_ds=True):
         """Seeds: device FP64 [4][ny][nx] (rho, ux, uy, T) and/or [16][ny][nx].
-        Returns (dL/ds numpy[16], dL/df0 device FP64 [16][ny][nx] or None)."""
+        Returns (dL/ds numpy[16] or None, dL/df0 device FP64 [16][ny][nx] or
+        None); without want_ds the rate gradients are not formed."""
         t = self.torch
         conv = lambda a: None if a is None else a.to(self.device, t.float64).contiguous()
         dm, df = conv(dL_dmacros), conv(dL_dfK)
         out = t.empty((16, self.cfg.ny, self.cfg.nx), dtype=t.float64, device=self.device) if want_df0 else None
-        ds = M.mrtlb_adjoint_backward(self.ctx, dm, df, out)
+        ds = M.mrtlb_adjoint_backward(self.ctx, dm, df, out, want_ds=want_ds)
         return ds, out
 
     def equilibrium_adjoint(self, dL_df, rho, ux, uy, T):

@@ -294,3 +294,29 @@ def test_autograd_refuses_an_overwritten_run(cuda):
         assert torch.isfinite(s.grad).all()
         with pytest.raises(RuntimeError, match="run or changed after this forward pass"):
             out1[3].sum().backward()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_backward_without_rate_gradients(cuda, kernel, precision):
+    """dL_ds = NULL skips the rate gradients' work in the adjoint steps; the
+    state adjoint dL/df0 is the same as with them, to the rounding of the
+    precision (the two kernel variants are compiled separately, so their
+    multiply-adds may contract differently)."""
+    import torch
+    cfg = _cfg(150, 37, BCS["walls_y"], precision=precision)
+    f0 = _state(cfg, 70)
+    if precision == "fp32":
+        f0 = f0.astype(np.float32)
+    w = torch.from_numpy(workloads.noise((16, cfg.ny, cfg.nx), 71)).to(cuda)
+    with Simulation(cfg) as sim:
+        sim.set_kernel(KERNELS[kernel])
+        sim.set_f(f0)
+        sim.adjoint_forward(4, interval=2)
+        ds, d1 = sim.adjoint_backward(dL_dfK=w)
+        none, d2 = sim.adjoint_backward(dL_dfK=w, want_ds=False)
+    assert none is None and np.abs(ds[4:]).max() > 0
+    a, b = d1.cpu().numpy(), d2.cpu().numpy()
+    scale = np.abs(a).reshape(16, -1).max(1)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert (np.abs(b - a).reshape(16, -1).max(1) / scale).max() < tol
