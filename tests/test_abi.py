@@ -116,3 +116,36 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             M.load(str(tmp_path / "libmrtlb.so"))
     finally:
         M._lib = saved
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """A C99 program (no C++) includes include/mrtlb.h under -pedantic
+    -Werror, links against libmrtlb.so and runs the calls that need no GPU:
+    argument errors and the error-string call."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text(r'''
+#include "mrtlb.h"
+#include <stdio.h>
+int main(void) {
+  mrtlb_ctx* ctx = NULL;
+  double out[5];
+  if (mrtlb_create(NULL, &ctx) != MRTLB_ERR_ARG) return 1;
+  if (mrtlb_step(NULL, 1) != MRTLB_ERR_ARG) return 2;
+  if (mrtlb_reduce(NULL, out) != MRTLB_ERR_ARG) return 3;
+  if (mrtlb_adjoint_pass(NULL) != 0) return 4;
+  if (mrtlb_last_error(NULL) == NULL) return 5;
+  printf("ok\n");
+  return 0;
+}
+''')
+    libdir = os.path.dirname(M.LIB_PATH)
+    exe = tmp_path / "use_header"
+    subprocess.run([cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", HEADER_DIR, str(src),
+                    "-L", libdir, "-lmrtlb", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
