@@ -253,8 +253,9 @@ int mrtlb_reduce_noalloc(const void* f, int nx, int ny, int precision, void* str
  * of all instances, plus one launch for the NEE walls of all instances that
  * have walls; runs of graph_steps steps (default 64) replay as CUDA graphs.
  * The instances' own calls (macros, get_f, reduce, ...) keep working on the
- * advanced states; stepping an instance alone while it is in a batch makes
- * the next mrtlb_batch_step return MRTLB_ERR_STATE.  The batch owns its
+ * advanced states; stepping an instance alone while it is in a batch, or
+ * binding it to other buffers, makes the next mrtlb_batch_step return
+ * MRTLB_ERR_STATE.  The batch owns its
  * tables and graphs, not the contexts.
  * ---------------------------------------------------------------------- */
 typedef struct mrtlb_batch mrtlb_batch;

@@ -234,6 +234,7 @@ void launch_batched_bx(const void* insts, const int4* tiles, int ntiles, int gri
 
 struct mrtlb_batch {
   std::vector<mrtlb_ctx*> ctx;
+  std::vector<void*> bufs;     // each instance's two state buffers as the tables hold them
   int prec = MRTLB_FP32;
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;  // capture stream (the legacy stream cannot be captured)
@@ -460,6 +461,8 @@ extern "C" int mrtlb_batch_create(mrtlb_ctx* const* ctxs, int n, mrtlb_batch** o
       return MRTLB_ERR_ARG;
     }
     b->ctx.push_back(c);
+    b->bufs.push_back(c->f[0]);
+    b->bufs.push_back(c->f[1]);
     b->nodes += (long long)c->L.nx * c->L.ny;
   }
   b->prec = ctxs[0]->prec;
@@ -530,8 +533,12 @@ extern "C" int mrtlb_batch_set_graph_steps(mrtlb_batch* b, int steps) {
 extern "C" int mrtlb_batch_step(mrtlb_batch* b, long nsteps) {
   TraceRange trace_("mrtlb_batch_step");
   if (!b || nsteps < 0) return MRTLB_ERR_ARG;
-  for (mrtlb_ctx* c : b->ctx)
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    const mrtlb_ctx* c = b->ctx[i];
+    if (c->f[0] != b->bufs[2 * i] || c->f[1] != b->bufs[2 * i + 1])
+      return bfail(b, MRTLB_ERR_STATE, "instance %d was bound to other buffers after the batch was made", (int)i);
     if (c->cur != b->cur) return bfail(b, MRTLB_ERR_STATE, "an instance was stepped or reset outside the batch");
+  }
   return run_steps(b, nsteps);
 }
 

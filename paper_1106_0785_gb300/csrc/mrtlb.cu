@@ -600,7 +600,9 @@ extern "C" int mrtlb_reduce(mrtlb_ctx* c, double out[5]) {
   if (rc) return rc;
   CK(cudaMemcpyAsync(out, c->acc, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy sums");
   rc = sync_and_check(c);
-  c->have_prev = 1;
+  // T_prev holds this call's temperatures unless the device work itself
+  // failed (a latched non-physical state or expired wait still let it run)
+  c->have_prev = (rc == MRTLB_OK || rc == MRTLB_ERR_NONPHYSICAL || rc == MRTLB_ERR_TIMEOUT) ? 1 : 0;
   return rc;
 }
 

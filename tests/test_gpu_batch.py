@@ -136,3 +136,24 @@ def test_batch_requires_matching_instances(cuda):
         with pytest.raises(M.MrtlbError) as ei:
             b.step(1)
         assert ei.value.code == M.MRTLB_ERR_STATE
+
+
+def test_batch_refuses_an_instance_bound_to_other_buffers(cuda):
+    """The batch's tables hold each instance's state buffers: binding an
+    instance to new buffers afterwards (which also resets its parity to the
+    batch's) makes the next batched step refuse rather than write through
+    the old pointers."""
+    import torch
+    a, fields = workloads.sod(nx=130, ny=5, precision="fp32")
+    s1, s2 = Simulation(a), Simulation(a)
+    for s in (s1, s2):
+        s.init_equilibrium(*fields)
+    with Batch([s1, s2]) as b:
+        b.step(2)
+        b.sync()
+        new = [torch.empty(s1.state_bytes, dtype=torch.uint8, device=cuda) for _ in range(2)]
+        M.mrtlb_bind(s1.ctx, new[0], new[1], s1.state_bytes)
+        s1.buffers = new
+        with pytest.raises(M.MrtlbError) as ei:
+            b.step(1)
+        assert ei.value.code == M.MRTLB_ERR_STATE
