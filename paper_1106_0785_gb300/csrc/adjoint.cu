@@ -101,13 +101,24 @@ __device__ __forceinline__ void adj_core_node(const R* __restrict__ ft, const R*
   const R ir = (rho > R(0)) ? adj_inv(rho) : R(0);
 #pragma unroll
   for (int q = 0; q < 16; ++q) lt[q] = R(0);
+  // (c) the modification at the neighbours, through u(p): with the
+  // collision's own u adjoint at an advanced node, else on its own
+  R uxb = R(0), uyb = R(0);
+  if (c.modified) {
+    uxb = c.inv2dx * (gbar_at(gsh, L, i - 1, j) - gbar_at(gsh, L, i + 1, j)) +
+          c.inv2dy * (gbar_at(gst, L, i, j - 1) - gbar_at(gst, L, i, j + 1));
+    uyb = c.inv2dx * (gbar_at(gst, L, i - 1, j) - gbar_at(gst, L, i + 1, j)) -
+          c.inv2dy * (gbar_at(gsh, L, i, j - 1) - gbar_at(gsh, L, i, j + 1));
+  }
   if (advanced<R>(L, i, j)) {
     R lp[16];
     load16(lam, P, at, lp);
     const long long aE = at + 1, aW = at - 1, aN = at + L.pitch, aS = at - L.pitch;
     const R shear = (Ux[aE] - Ux[aW]) * c.inv2dx - (Uy[aN] - Uy[aS]) * c.inv2dy;
     const R strain = (Uy[aE] - Uy[aW]) * c.inv2dx + (Ux[aN] - Ux[aS]) * c.inv2dy;
-    collision_T_node<R, RATES>(a, g, lp, ux, uy, shear, strain, lt, G);
+    collision_T_node<R, RATES>(a, g, lp, ux, uy, shear, strain, uxb, uyb, lt, G);
+  } else if (c.modified) {
+    velocity_T(uxb, uyb, ux, uy, ir, lt);
   }
   // (a) neighbours' Lax-Wendroff weights on p
   const int nbi[4] = {i - 1, i + 1, i, i};  // r = p - e_x (uses kE), p + e_x (kW), p - e_y (kN), p + e_y (kS)
@@ -122,14 +133,6 @@ __device__ __forceinline__ void adj_core_node(const R* __restrict__ ft, const R*
       if (n >= 2 && vy_of(q) == 0) continue;
       lt[q] += c.lw[q][n] * lam[q * P + ar];
     }
-  }
-  // (c) the modification at the neighbours, through u(p)
-  if (c.modified) {
-    const R uxb = c.inv2dx * (gbar_at(gsh, L, i - 1, j) - gbar_at(gsh, L, i + 1, j)) +
-                  c.inv2dy * (gbar_at(gst, L, i, j - 1) - gbar_at(gst, L, i, j + 1));
-    const R uyb = c.inv2dx * (gbar_at(gst, L, i - 1, j) - gbar_at(gst, L, i + 1, j)) -
-                  c.inv2dy * (gbar_at(gsh, L, i, j - 1) - gbar_at(gsh, L, i, j + 1));
-    velocity_T(uxb, uyb, ux, uy, ir, lt);
   }
 #pragma unroll
   for (int q = 0; q < 16; ++q) out[q * P + at] = lt[q];

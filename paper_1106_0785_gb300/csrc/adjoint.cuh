@@ -257,9 +257,13 @@ __device__ __forceinline__ void gbar_node(const Coef<R>& c, const R lam[16], R P
 // collision transpose, the temperature linearised at T = (e - j.u/2)/rho),
 // and the rate gradients of the node added to G[4..15] (RATES = false
 // skips them and the moments and equilibria only they need; lt is the same).
+// uxb, uyb: the adjoint of u(p) from elsewhere (the modification at the
+// neighbours); it joins the collision's own u adjoint and goes back to f
+// through u = j / rho with it, which is velocity_T folded into the moments
+// (rows 1, v_x, v_y of M).
 template <typename R, bool RATES = true>
 __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[16], const R lp[16], R ux, R uy,
-                                                 R shear, R strain, R lt[16], R G[16]) {
+                                                 R shear, R strain, R uxb, R uyb, R lt[16], R G[16]) {
   const Coef<R>& c = a.c;
   R rho, jx, jy, e;
   conserved(g, rho, jx, jy, e);
@@ -286,7 +290,7 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
     eqb[k] = (k >= 4) ? -c.rate[k] * cb[k] : R(0);
   }
   EqIn<R> x{rho, ir, jx, jy, e, ux, uy, T};
-  EqIn<R> gi{R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+  EqIn<R> gi{R(0), R(0), R(0), R(0), R(0), uxb, uyb, R(0)};
   if (c.modified) {
     const R Pb = cb[6] * (c.mod[0] * ux * shear + c.mod[1] * uy * strain) +
                  cb[7] * (c.mod[2] * ux * strain + c.mod[3] * uy * shear);

@@ -148,6 +148,13 @@ struct AdjMarch {
     R lt[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) lt[q] = R(0);
+    // the modification at the neighbours, through u(p)
+    R uxb = R(0), uyb = R(0);
+    if (c.modified) {
+      const int G0 = 2 * SM::PW, G1 = 3 * SM::PW;
+      uxb = c.inv2dx * (pc[G0 + i1 - 1] - pc[G0 + i1 + 1]) + c.inv2dy * (pp[G1 + i1] - pn[G1 + i1]);
+      uyb = c.inv2dx * (pc[G1 + i1 - 1] - pc[G1 + i1 + 1]) - c.inv2dy * (pp[G0 + i1] - pn[G0 + i1]);
+    }
     const bool rC = row_adv(j);
     if (colC && rC) {
       const R* fr = frow(j);
@@ -159,7 +166,9 @@ struct AdjMarch {
       }
       const R shear = (pc[i1 + 1] - pc[i1 - 1]) * c.inv2dx - (pn[SM::PW + i1] - pp[SM::PW + i1]) * c.inv2dy;
       const R strain = (pc[SM::PW + i1 + 1] - pc[SM::PW + i1 - 1]) * c.inv2dx + (pn[i1] - pp[i1]) * c.inv2dy;
-      collision_T_node<R, RATES>(a, g, lp, ux, uy, shear, strain, lt, G);
+      collision_T_node<R, RATES>(a, g, lp, ux, uy, shear, strain, uxb, uyb, lt, G);
+    } else if (c.modified) {
+      velocity_T(uxb, uyb, ux, uy, pc[4 * SM::PW + i1], lt);
     }
     // neighbours' Lax-Wendroff weights: r = p - e_x (k_E), p + e_x (k_W), p - e_y (k_N), p + e_y (k_S)
     const bool aW = colW && rC, aE = colE && rC;
@@ -174,13 +183,6 @@ struct AdjMarch {
         if (aS) lt[q] += c.lw[q][2] * lp_[q * SM::BW + bc];
         if (aN) lt[q] += c.lw[q][3] * ln[q * SM::BW + bc];
       }
-    }
-    // the modification at the neighbours, through u(p)
-    if (c.modified) {
-      const int G0 = 2 * SM::PW, G1 = 3 * SM::PW;
-      const R uxb = c.inv2dx * (pc[G0 + i1 - 1] - pc[G0 + i1 + 1]) + c.inv2dy * (pp[G1 + i1] - pn[G1 + i1]);
-      const R uyb = c.inv2dx * (pc[G1 + i1 - 1] - pc[G1 + i1 + 1]) - c.inv2dy * (pp[G0 + i1] - pn[G0 + i1]);
-      velocity_T(uxb, uyb, ux, uy, pc[4 * SM::PW + i1], lt);
     }
     {
       R* o = out + L.node(x, j);
