@@ -208,7 +208,6 @@ static int build_coefficients(mrtlb_ctx* c) {
   Coef<float>& f = c->c32;
   f.a1x = (float)k.a1x; f.b1x = (float)k.b1x; f.a1y = (float)k.a1y; f.b1y = (float)k.b1y;
   f.inv2dx = (float)k.inv2dx; f.inv2dy = (float)k.inv2dy;
-  for (int q = 0; q < 16; ++q)
   for (int q = 0; q < 16; ++q) {
     double w[4] = {k.lw[q][0], k.lw[q][1], k.lw[q][2], k.lw[q][3]}, sum;
     on_common_grid(w, 23, &sum);
