@@ -255,7 +255,10 @@ int mrtlb_reduce_noalloc(const void* f, int nx, int ny, int precision, void* str
  * The instances' own calls (macros, get_f, reduce, ...) keep working on the
  * advanced states; stepping an instance alone while it is in a batch, or
  * binding it to other buffers, makes the next mrtlb_batch_step return
- * MRTLB_ERR_STATE.  The batch owns its
+ * MRTLB_ERR_STATE.  Rates set on an instance with mrtlb_set_rates take
+ * effect at the next mrtlb_batch_step (or mrtlb_batch_tune), which copies
+ * the instances' coefficient blocks into the batch's tables again (after
+ * the steps already queued).  The batch owns its
  * tables and graphs, not the contexts.
  * ---------------------------------------------------------------------- */
 typedef struct mrtlb_batch mrtlb_batch;

@@ -684,10 +684,17 @@ int forward_impl(mrtlb_ctx* c, long K) {
   // a previous pass of the same shape keeps its buffers and plans
   mrtlb_adjoint_state* a = old;
   if (!(old && old->S == S && (long)old->ckpt.size() >= nck && old->kernel == c->kernel)) {
+    if (old) cudaStreamSynchronize(st);  // (its buffers may still be in use by queued work)
     release(old);
     c->adj = a = new mrtlb_adjoint_state();
     const int rc = allocate<R>(c, a, S, nck);
-    if (rc) return rc;
+    if (rc) {  // (no half-built state stays behind for a later pass to reuse)
+      cudaGetLastError();  // (reported here; the next launch check must not see it again)
+      cudaStreamSynchronize(st);
+      release(a);
+      c->adj = nullptr;
+      return rc;
+    }
   }
   a->K = K;
   a->nseg = nseg;

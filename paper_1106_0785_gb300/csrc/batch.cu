@@ -235,6 +235,7 @@ void launch_batched_bx(const void* insts, const int4* tiles, int ntiles, int gri
 struct mrtlb_batch {
   std::vector<mrtlb_ctx*> ctx;
   std::vector<void*> bufs;     // each instance's two state buffers as the tables hold them
+  std::vector<double> rates;   // each instance's s[16] as the tables' coefficient blocks hold them
   int prec = MRTLB_FP32;
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;  // capture stream (the legacy stream cannot be captured)
@@ -362,6 +363,57 @@ int set_tiles(mrtlb_batch* b, int bx, int seglen) {
   return MRTLB_OK;
 }
 
+// Wall table: one entry per instance with walls (its layout, coefficient
+// blocks, wall data and buffers) and the running count of its wall nodes.
+// Allocated on the first call; later calls rewrite it in place.
+int upload_walls(mrtlb_batch* b) {
+  std::vector<WallInst> w;
+  int first = 0;
+  for (int i = 0; i < (int)b->ctx.size(); ++i) {
+    const int nwall = wall_count(b->ctx[i]->L);
+    if (nwall == 0) continue;
+    WallInst e;
+    std::memset(&e, 0, sizeof(e));
+    e.L = b->ctx[i]->L;
+    e.c32 = b->ctx[i]->c32;
+    e.c64 = b->ctx[i]->c64;
+    e.w = b->ctx[i]->walls;
+    e.f[0] = b->ctx[i]->f[0];
+    e.f[1] = b->ctx[i]->f[1];
+    e.first = first;
+    first += nwall;
+    w.push_back(e);
+  }
+  b->nwall_inst = (int)w.size();
+  b->total_walls = first;
+  if (w.empty()) return MRTLB_OK;
+  if (!b->d_walls) BCK(cudaMalloc((void**)&b->d_walls, w.size() * sizeof(WallInst)), "cudaMalloc(wall table)");
+  BCK(cudaMemcpy(b->d_walls, w.data(), w.size() * sizeof(WallInst), cudaMemcpyHostToDevice), "copy wall table");
+  return MRTLB_OK;
+}
+
+void snapshot_rates(mrtlb_batch* b) {
+  b->rates.resize(16 * b->ctx.size());
+  for (size_t i = 0; i < b->ctx.size(); ++i) std::memcpy(&b->rates[16 * i], b->ctx[i]->s, 16 * sizeof(double));
+}
+
+// Rates set on an instance (mrtlb_set_rates) after its coefficient blocks
+// were copied into the tables: copy them again, in place (the captured
+// time loops read the tables when they run, so they stay valid).
+int refresh_coefficients(mrtlb_batch* b) {
+  bool changed = false;
+  for (size_t i = 0; i < b->ctx.size() && !changed; ++i)
+    changed = std::memcmp(&b->rates[16 * i], b->ctx[i]->s, 16 * sizeof(double)) != 0;
+  if (!changed) return MRTLB_OK;
+  BCK(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");  // queued steps read the old blocks
+  int rc = (b->prec == MRTLB_FP64) ? upload_instances<double>(b, b->bx, coef64)
+                                   : upload_instances<float>(b, b->bx, coef32);
+  if (!rc) rc = upload_walls(b);
+  if (rc) return rc;
+  snapshot_rates(b);
+  return MRTLB_OK;
+}
+
 void enqueue_batch_step(mrtlb_batch* b, int cur, cudaStream_t st) {
   if (b->total_walls > 0) {
     const int nb = (b->total_walls + 127) / 128;
@@ -478,33 +530,11 @@ extern "C" int mrtlb_batch_create(mrtlb_ctx* const* ctxs, int n, mrtlb_batch** o
   if (cudaMalloc((void**)&b->claim, 2 * sizeof(int)) != cudaSuccess ||
       cudaMemset(b->claim, 0, 2 * sizeof(int)) != cudaSuccess)
     return cleanup(MRTLB_ERR_CUDA);
-  // wall table
-  std::vector<WallInst> w;
-  int first = 0;
-  for (int i = 0; i < n; ++i) {
-    const int nwall = wall_count(b->ctx[i]->L);
-    if (nwall == 0) continue;
-    WallInst e;
-    std::memset(&e, 0, sizeof(e));
-    e.L = b->ctx[i]->L;
-    e.c32 = b->ctx[i]->c32;
-    e.c64 = b->ctx[i]->c64;
-    e.w = b->ctx[i]->walls;
-    e.f[0] = b->ctx[i]->f[0];
-    e.f[1] = b->ctx[i]->f[1];
-    e.first = first;
-    first += nwall;
-    w.push_back(e);
-  }
-  b->nwall_inst = (int)w.size();
-  b->total_walls = first;
-  if (!w.empty()) {
-    if (cudaMalloc((void**)&b->d_walls, w.size() * sizeof(WallInst)) != cudaSuccess ||
-        cudaMemcpy(b->d_walls, w.data(), w.size() * sizeof(WallInst), cudaMemcpyHostToDevice) != cudaSuccess)
-      return cleanup(MRTLB_ERR_CUDA);
-  }
-  const int rc = set_tiles(b, b->prec == MRTLB_FP64 ? 64 : 128, 32);
+  int rc = upload_walls(b);
   if (rc) return cleanup(rc);
+  rc = set_tiles(b, b->prec == MRTLB_FP64 ? 64 : 128, 32);
+  if (rc) return cleanup(rc);
+  snapshot_rates(b);
   *out = b;
   return MRTLB_OK;
 }
@@ -539,6 +569,8 @@ extern "C" int mrtlb_batch_step(mrtlb_batch* b, long nsteps) {
       return bfail(b, MRTLB_ERR_STATE, "instance %d was bound to other buffers after the batch was made", (int)i);
     if (c->cur != b->cur) return bfail(b, MRTLB_ERR_STATE, "an instance was stepped or reset outside the batch");
   }
+  const int rc = refresh_coefficients(b);
+  if (rc) return rc;
   return run_steps(b, nsteps);
 }
 
@@ -558,6 +590,10 @@ extern "C" int mrtlb_batch_tune(mrtlb_batch* b, const char* cache_path, int tria
                                 int* seglen_out) {
   if (!b) return MRTLB_ERR_ARG;
   if (trial_steps < 1) trial_steps = 8;
+  {
+    const int rc = refresh_coefficients(b);  // (the trials step with the instances' current rates)
+    if (rc) return rc;
+  }
   const std::string sig = signature(b);
   // cached?
   if (cache_path && cache_path[0]) {

@@ -320,3 +320,34 @@ def test_backward_without_rate_gradients(cuda, kernel, precision):
     scale = np.abs(a).reshape(16, -1).max(1)
     tol = 1e-12 if precision == "fp64" else 1e-5
     assert (np.abs(b - a).reshape(16, -1).max(1) / scale).max() < tol
+
+
+def test_forward_pass_that_cannot_allocate_keeps_nothing(cuda):
+    """A forward pass whose segment of states cannot be allocated (segments
+    of a million states: about 2 TB here, far beyond the device) fails with
+    MRTLB_ERR_CUDA after its checkpoints were allocated and before any step
+    runs, and keeps nothing: no backward pass is possible, the same request
+    fails the same way again (instead of reusing the half-built buffers),
+    and a pass that fits then gives what a fresh context gives."""
+    import torch
+    cfg = _cfg(300, 40, BCS["outflow_x"])
+    f0 = _state(cfg, 180)
+    w = torch.from_numpy(np.random.default_rng(181).standard_normal(f0.shape)).to(cuda)
+    with Simulation(cfg) as sim:
+        sim.set_f(f0)
+        for _ in range(2):
+            with pytest.raises(M.MrtlbError) as e:
+                sim.adjoint_forward(2_000_000, interval=1_000_000)
+            assert e.value.code == M.MRTLB_ERR_CUDA
+            assert sim.adjoint_pass() == 0
+            assert sim.steps == 0
+        with pytest.raises(M.MrtlbError) as e:
+            sim.adjoint_backward(dL_dfK=w)
+        assert e.value.code == M.MRTLB_ERR_STATE
+        sim.adjoint_forward(5, interval=0)
+        _, l1 = sim.adjoint_backward(dL_dfK=w)
+    with Simulation(cfg) as fresh:
+        fresh.set_f(f0)
+        fresh.adjoint_forward(5)
+        _, l2 = fresh.adjoint_backward(dL_dfK=w)
+    assert np.array_equal(l1.cpu().numpy(), l2.cpu().numpy())

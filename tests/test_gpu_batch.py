@@ -157,3 +157,37 @@ def test_batch_refuses_an_instance_bound_to_other_buffers(cuda):
         with pytest.raises(M.MrtlbError) as ei:
             b.step(1)
         assert ei.value.code == M.MRTLB_ERR_STATE
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_follows_rates_set_on_an_instance(cuda, precision):
+    """The batch's tables hold each instance's coefficient blocks: rates set
+    on an instance with mrtlb_set_rates after the batch was made (here on a
+    Couette channel with walls, whose wall table holds them too) take effect
+    at the next batched step, inside the captured time loop, as they do for
+    the instance stepped alone."""
+    insts = [workloads.sod(nx=300, ny=5, precision=precision),
+             workloads.couette(Pr=0.5, nx=130, ny=12, precision=precision, U=0.4)]
+    ref = _sims(insts, M.MRTLB_KERNEL_TILED)
+    sims = _sims(insts)
+    for s in ref:
+        s.step(13)
+    with Batch(sims) as b:
+        b.set_graph_steps(8)
+        b.step(13)
+        b.sync()
+        for group in (ref, sims):
+            s = np.array(group[1].rates())
+            s[6:8] *= 4.0  # Pr 0.5 -> 2 (s7, s8)
+            s[4:6] *= 0.5
+            group[1].set_rates(s)
+        for s in ref:
+            s.step(19)
+        b.step(19)
+        b.sync()
+    for s, r in zip(sims, ref):
+        assert _rel(s.get_f(), r.get_f()) < (1e-13 if precision == "fp64" else 1e-6)
+    # and the change matters: the channel stepped without it differs
+    other = _sims(insts[1:], M.MRTLB_KERNEL_TILED)[0]
+    other.step(32)
+    assert _rel(other.get_f(), ref[1].get_f()) > 1e-6
