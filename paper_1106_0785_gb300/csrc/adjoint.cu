@@ -453,17 +453,24 @@ void launch_adj_march(const mrtlb_adjoint_state* a, const Layout& L, const CUten
   constexpr int BX = AdjTile<R>::BX, NF = AdjTile<R>::NF, NL = AdjTile<R>::NL;
   using SM = AdjSmem<R, BX, NF, NL>;
   static const bool attr = [] {  // once per instantiation (thread-safe static initialisation)
-    return cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SM::bytes) == cudaSuccess &&
-           cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SM::bytes) == cudaSuccess;
+    const int b = (int)SM::bytes;
+    const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    return cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true, 0>, A, b) == cudaSuccess &&
+           cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false, 0>, A, b) == cudaSuccess &&
+           cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true, 1>, A, b) == cudaSuccess &&
+           cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false, 1>, A, b) == cudaSuccess;
   }();
   (void)attr;
   dim3 grid(a->m_nstrips, a->m_nseg);
-  if (rates)
-    adj_march_kernel<R, BX, NF, NL, true><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
+  const bool v1 = ac.c.version == 1;  // (version 1 has its own kernels, without the others' transposes)
+  if (rates && v1)
+    adj_march_kernel<R, BX, NF, NL, true, 1><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
+  else if (rates)
+    adj_march_kernel<R, BX, NF, NL, true, 0><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
+  else if (v1)
+    adj_march_kernel<R, BX, NF, NL, false, 1><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
   else
-    adj_march_kernel<R, BX, NF, NL, false><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
+    adj_march_kernel<R, BX, NF, NL, false, 0><<<grid, BX, SM::bytes, st>>>(fm, lm, out, L, ac, a->gacc, err, a->m_seglen);
 }
 
 // one adjoint step: lambda[li] (dL/df^{n+1}) -> lambda[li ^ 1] (dL/df^n),
@@ -514,15 +521,17 @@ bool plan_adj_march(mrtlb_ctx* c, mrtlb_adjoint_state* a) {
     if (encode_row_maps(L, es, s0, s1, BX, &a->fmap[n]) != 0) return false;
   }
   if (encode_row_maps(L, es, a->lam[0], a->lam[1], BX, a->lmap) != 0) return false;
-  if (cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SM::bytes) != cudaSuccess ||
-      cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SM::bytes) != cudaSuccess)
+  const int b = (int)SM::bytes;
+  const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true, 0>, A, b) != cudaSuccess ||
+      cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false, 0>, A, b) != cudaSuccess ||
+      cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true, 1>, A, b) != cudaSuccess ||
+      cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false, 1>, A, b) != cudaSuccess)
     return false;
   int dev = 0, nsm = 1, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj_march_kernel<R, BX, NF, NL, true>, BX, SM::bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, adj_march_kernel<R, BX, NF, NL, true, 0>, BX, SM::bytes);
   if (per < 1) return false;
   const int rows = L.ny + 2;  // output rows -1 .. ny
   a->m_nstrips = (L.nx + 2 + SM::SX - 1) / SM::SX;

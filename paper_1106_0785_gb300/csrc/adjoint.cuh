@@ -101,8 +101,9 @@ struct EqIn {
   R rho, ir, jx, jy, e, ux, uy, T;
 };
 
-// transpose of equilibrium(): eqb[16] (all rows) -> adjoints of its inputs.
-template <typename R>
+// transpose of equilibrium(): eqb[16] (all rows) -> adjoints of its inputs
+// (VER: the equilibrium version fixed at compile time, 0 = c.version).
+template <typename R, int VER = 0>
 __device__ __forceinline__ void equilibrium_T(const Coef<R>& c, const EqIn<R>& x, const R eqb[16],
                                               EqIn<R>& g) {
   const R ux = x.ux, uy = x.uy, ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
@@ -136,14 +137,15 @@ __device__ __forceinline__ void equilibrium_T(const Coef<R>& c, const EqIn<R>& x
   wb += eqb[12] * (ux2 - uy2) + eqb[13] * ux * uy;
   g.ux += eqb[12] * w * R(2) * ux + eqb[13] * w * uy;
   g.uy += -eqb[12] * w * R(2) * uy + eqb[13] * w * ux;
-  if (c.version == 2) {
+  const int ver = VER ? VER : c.version;
+  if (ver == 2) {
     const R A = R(-4) + R(10) * x.T + R(5) * ux2 - R(5) * uy2;
     const R B = R(4) - R(10) * x.T + R(5) * ux2 - R(5) * uy2;
     g.rho += eqb[14] * ux * A + eqb[15] * uy * B;
     g.ux += eqb[14] * x.rho * (A + R(10) * ux2) + eqb[15] * x.rho * uy * R(10) * ux;
     g.uy += -eqb[14] * x.rho * ux * R(10) * uy + eqb[15] * x.rho * (B - R(10) * uy2);
     g.T += R(10) * x.rho * (eqb[14] * ux - eqb[15] * uy);
-  } else if (c.version == 3) {
+  } else if (ver == 3) {
     // rows 12, 15, 16 of M applied to f_M,q = rho/(2 pi T) exp(-|v_q - u|^2 / 2T):
     // their adjoints go back through the harmonics to f_M, then through
     // d f_M,q = f_M,q (drho / rho + (v_q - u).du / T + (|v_q - u|^2 / 2T^2 - 1/T) dT)
@@ -260,8 +262,9 @@ __device__ __forceinline__ void gbar_node(const Coef<R>& c, const R lam[16], R P
 // uxb, uyb: the adjoint of u(p) from elsewhere (the modification at the
 // neighbours); it joins the collision's own u adjoint and goes back to f
 // through u = j / rho with it, which is velocity_T folded into the moments
-// (rows 1, v_x, v_y of M).
-template <typename R, bool RATES = true>
+// (rows 1, v_x, v_y of M).  VER: the equilibrium version fixed at compile
+// time (0 = c.version).
+template <typename R, bool RATES = true, int VER = 0>
 __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[16], const R lp[16], R ux, R uy,
                                                  R shear, R strain, R uxb, R uyb, R lt[16], R G[16]) {
   const Coef<R>& c = a.c;
@@ -276,7 +279,7 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
     Harm<R> h;
     harmonics(g, h);
     moments(h, m);
-    equilibrium(c, rho, ir, jx, jy, e, ux, uy, T, eq);
+    equilibrium<R, VER>(c, rho, ir, jx, jy, e, ux, uy, T, eq);
   }
   const R Pp = rho * T;
   R Cb[16], cb[16];
@@ -299,7 +302,7 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
     gi.rho += Pb * T;
     gi.T += Pb * rho;
   }
-  equilibrium_T(c, x, eqb, gi);
+  equilibrium_T<R, VER>(c, x, eqb, gi);
   R rb, jxb, jyb, eb;
   chain_primitive(x, gi, rb, jxb, jyb, eb);
   mb[0] += rb;
@@ -314,16 +317,17 @@ __device__ __forceinline__ void collision_T_node(const AdjCoef<R>& a, const R g[
   for (int q = 0; q < 16; ++q) lt[q] += fb[q];
   // rate gradients over dt: d f1 / d s_k through dt s_k (m_k - eq_k) and
   // the modification factors dt (s7/s5 - 1), ... (dL/dC = -lambda)
-  if constexpr (!RATES) return;
+  if constexpr (RATES) {
 #pragma unroll
-  for (int k = 4; k < 16; ++k) G[k] += cb[k] * (m[k] - eq[k]);
-  if (c.modified) {
-    const R A0 = Pp * ux * shear, A1 = Pp * uy * strain;
-    const R A2 = Pp * ux * strain, A3 = Pp * uy * shear;
-    G[6] += cb[6] * (A0 * a.g[0] + A1 * a.g[1]);        // 1/s5, 1/s6
-    G[7] += cb[7] * (A2 * a.g[1] + A3 * a.g[0]);
-    G[4] -= cb[6] * A0 * a.g[2] + cb[7] * A3 * a.g[4];  // s7/s5^2, s8/s5^2
-    G[5] -= cb[6] * A1 * a.g[3] + cb[7] * A2 * a.g[5];  // s7/s6^2, s8/s6^2
+    for (int k = 4; k < 16; ++k) G[k] += cb[k] * (m[k] - eq[k]);
+    if (c.modified) {
+      const R A0 = Pp * ux * shear, A1 = Pp * uy * strain;
+      const R A2 = Pp * ux * strain, A3 = Pp * uy * shear;
+      G[6] += cb[6] * (A0 * a.g[0] + A1 * a.g[1]);        // 1/s5, 1/s6
+      G[7] += cb[7] * (A2 * a.g[1] + A3 * a.g[0]);
+      G[4] -= cb[6] * A0 * a.g[2] + cb[7] * A3 * a.g[4];  // s7/s5^2, s8/s5^2
+      G[5] -= cb[6] * A1 * a.g[3] + cb[7] * A2 * a.g[5];  // s7/s6^2, s8/s6^2
+    }
   }
 }
 

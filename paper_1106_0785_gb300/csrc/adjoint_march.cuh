@@ -133,7 +133,7 @@ struct AdjMarch {
   }
 
   // lambda~ of output node (x, j); the rate gradients of the node go to G
-  template <bool RATES>
+  template <bool RATES, int VER>
   __device__ __forceinline__ void core(const AdjCoef<R>& a, int j, R G[16]) const {
     const Coef<R>& c = a.c;
     const int bc = SM::HL - 2 + t;  // box column of x
@@ -166,7 +166,7 @@ struct AdjMarch {
       }
       const R shear = (pc[i1 + 1] - pc[i1 - 1]) * c.inv2dx - (pn[SM::PW + i1] - pp[SM::PW + i1]) * c.inv2dy;
       const R strain = (pc[SM::PW + i1 + 1] - pc[SM::PW + i1 - 1]) * c.inv2dx + (pn[i1] - pp[i1]) * c.inv2dy;
-      collision_T_node<R, RATES>(a, g, lp, ux, uy, shear, strain, uxb, uyb, lt, G);
+      collision_T_node<R, RATES, VER>(a, g, lp, ux, uy, shear, strain, uxb, uyb, lt, G);
     } else if (c.modified) {
       velocity_T(uxb, uyb, ux, uy, pc[4 * SM::PW + i1], lt);
     }
@@ -193,7 +193,7 @@ struct AdjMarch {
 
   // Output rows [ja, jb) of the strip at x0 (a multiple of BX).  Returns
   // true if a wait expired (the CTA agreed to stop).
-  template <bool RATES>
+  template <bool RATES, int VER>
   __device__ __forceinline__ bool segment(const AdjCoef<R>& a, int ja, int jb, R G[16]) {
     x = x0 - 2 + t;
     out_col = t >= 1 && t <= SM::SX && x <= L.nx;
@@ -219,7 +219,7 @@ struct AdjMarch {
       if (!bad) prep(a, j + 1);
       if (__syncthreads_or(bad)) return true;
       refill(j - 1, j - 2);
-      if (out_col) core<RATES>(a, j, G);
+      if (out_col) core<RATES, VER>(a, j, G);
     }
     return false;
   }
@@ -238,7 +238,11 @@ struct AdjMarch {
 // One CTA per (strip, row segment): strips x0 = blockIdx.x * SX, output
 // rows -1 + blockIdx.y * seglen ... (clipped at ny + 1).
 // (FP32: three CTAs per SM, the shared-memory limit, so at most 170 registers)
-template <typename R, int BX, int NF, int NL, bool RATES>
+// VER: the equilibrium version fixed at compile time (1), or 0 to follow the
+// coefficients' (the version-2 and -3 transposes then stay out of the
+// version-1 kernels: 111 instead of 168 registers in FP32 with the rate
+// gradients, and fewer instruction-fetch stalls).
+template <typename R, int BX, int NF, int NL, bool RATES, int VER>
 __global__ void __launch_bounds__(BX, sizeof(R) == 4 ? 3 : 1)
     adj_march_kernel(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap lmap,
                      R* __restrict__ out, const Layout L, const __grid_constant__ AdjCoef<R> a, double* gacc,
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(BX, sizeof(R) == 4 ? 3 : 1)
   R G[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) G[k] = R(0);
-  if (m.template segment<RATES>(a, ja, jb, G)) {
+  if (m.template segment<RATES, VER>(a, ja, jb, G)) {
     if (m.t == 0) atomicOr(err, ERRBIT_TIMEOUT);
     m.drain();
   }

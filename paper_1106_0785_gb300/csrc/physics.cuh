@@ -261,7 +261,7 @@ __device__ __forceinline__ double expr(double x) { return exp(x); }
 
 // Equilibrium moments k = 4..15 (Eqs. 14a-14i and the version rule for
 // k = 11, 14, 15), given the conserved moments and u, T.
-template <typename R>
+template <typename R, int VER = 0>
 MRTLB_HD void equilibrium(const Coef<R>& c, R rho, R inv_rho, R jx, R jy, R e,
                                             R ux, R uy, R T, R eq[16]) {
   const R ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
@@ -277,11 +277,12 @@ MRTLB_HD void equilibrium(const Coef<R>& c, R rho, R inv_rho, R jx, R jy, R e,
   const R w = R(6) * e - R(2) * rho * u2;
   eq[12] = w * (ux2 - uy2);                       // 14h
   eq[13] = w * ux * uy;                           // 14i
-  if (c.version == 2) {
+  const int ver = VER ? VER : c.version;          // (VER: fixed at compile time)
+  if (ver == 2) {
     eq[11] = R(0);
     eq[14] = rho * ux * (R(-4) + R(10) * T + R(5) * ux2 - R(5) * uy2);
     eq[15] = rho * uy * (R(4) - R(10) * T + R(5) * ux2 - R(5) * uy2);
-  } else if (c.version == 3) {
+  } else if (ver == 3) {
     // rows 12, 15, 16 of M applied to rho/(2 pi T) exp(-(v - u)^2 / 2T)
     R fm[16];
     const R pre = rho * recip(R(6.283185307179586476925286766559) * T);
