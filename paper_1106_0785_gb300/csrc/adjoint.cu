@@ -452,15 +452,7 @@ void launch_adj_march(const mrtlb_adjoint_state* a, const Layout& L, const CUten
                       R* out, const AdjCoef<R>& ac, int* err, bool rates, cudaStream_t st) {
   constexpr int BX = AdjTile<R>::BX, NF = AdjTile<R>::NF, NL = AdjTile<R>::NL;
   using SM = AdjSmem<R, BX, NF, NL>;
-  static const bool attr = [] {  // once per instantiation (thread-safe static initialisation)
-    const int b = (int)SM::bytes;
-    const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    return cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true, 0>, A, b) == cudaSuccess &&
-           cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false, 0>, A, b) == cudaSuccess &&
-           cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, true, 1>, A, b) == cudaSuccess &&
-           cudaFuncSetAttribute(adj_march_kernel<R, BX, NF, NL, false, 1>, A, b) == cudaSuccess;
-  }();
-  (void)attr;
+  // (plan_adj_march allowed the kernels' dynamic shared memory in this context)
   dim3 grid(a->m_nstrips, a->m_nseg);
   const bool v1 = ac.c.version == 1;  // (version 1 has its own kernels, without the others' transposes)
   if (rates && v1)

@@ -205,25 +205,27 @@ template <> struct BatchShapes<double> {
 #define MRTLB_PAIR 1
 #endif
 
+// The dynamic shared memory the batched kernel of this shape needs, allowed
+// for it in the current context (set by set_tiles, so once per batch and
+// tile shape, on the batch's device, outside any stream capture).
+template <typename R, int BX, int MINB>
+cudaError_t allow_batched_smem() {
+  constexpr int NS = BatchShapes<R>::NS;
+  const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if constexpr (sizeof(R) == 4 && MRTLB_PAIR)
+    return cudaFuncSetAttribute(step_batched_pair_kernel<BX, NS, MINB>, A, (int)batch_pair_smem<BX, NS>());
+  else
+    return cudaFuncSetAttribute(step_batched_kernel<R, BX, NS, MINB>, A, (int)batch_smem<R, BX, NS>());
+}
+
 template <typename R, int BX, int MINB>
 void launch_batched_bx(const void* insts, const int4* tiles, int ntiles, int grid, int cur, int* err, int* claim,
                        cudaStream_t st) {
   constexpr int NS = BatchShapes<R>::NS;
   if constexpr (sizeof(R) == 4 && MRTLB_PAIR) {
-    static const bool attr = [] {  // once per instantiation (thread-safe static initialisation)
-      return cudaFuncSetAttribute(step_batched_pair_kernel<BX, NS, MINB>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)batch_pair_smem<BX, NS>()) == cudaSuccess;
-    }();
-    (void)attr;
     step_batched_pair_kernel<BX, NS, MINB><<<grid, BX / 2, batch_pair_smem<BX, NS>(), st>>>(
         (const BatchInst<float>*)insts, tiles, ntiles, cur, err, claim);
   } else {
-    static const bool attr = [] {
-      return cudaFuncSetAttribute(step_batched_kernel<R, BX, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)batch_smem<R, BX, NS>()) == cudaSuccess;
-    }();
-    (void)attr;
     step_batched_kernel<R, BX, NS, MINB><<<grid, BX, batch_smem<R, BX, NS>(), st>>>(
         (const BatchInst<R>*)insts, tiles, ntiles, cur, err);
   }
@@ -321,6 +323,12 @@ void drop_graphs(mrtlb_batch* b) {
 int set_tiles(mrtlb_batch* b, int bx, int seglen) {
   if (!shape_supported(b->prec, bx)) return bfail(b, MRTLB_ERR_ARG, "strip width %d not available", bx);
   if (seglen < 1) return bfail(b, MRTLB_ERR_ARG, "segment length %d", seglen);
+  {
+    const cudaError_t e = (b->prec == MRTLB_FP64) ? allow_batched_smem<double, 64, 3>()
+                          : (bx == 64)            ? allow_batched_smem<float, 64, MRTLB_BATCH_MINB64>()
+                                                  : allow_batched_smem<float, 128, MRTLB_BATCH_MINB128>();
+    if (e != cudaSuccess) return bfail(b, MRTLB_ERR_CUDA, "shared-memory attribute: %s", cudaGetErrorString(e));
+  }
   if (bx != b->bx) {
     cudaStreamSynchronize(b->stream);  // the table may be in use by queued steps
     const int rc = (b->prec == MRTLB_FP64) ? upload_instances<double>(b, bx, coef64)

@@ -200,6 +200,25 @@ int plan_tiled(const Layout& L, int esize, void* f0, void* f1, TiledPlan* plan) 
     plan->smem = PairSmem<BX, NS>::bytes;
   }
   if (per_sm < 1) per_sm = 1;
+  // the dynamic shared memory of the kernel launch_step_tiled will launch,
+  // allowed in the current context (here: once per bind, on the bound
+  // device, outside any stream capture)
+  {
+    const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    constexpr int BXf = Tile<float>::BX, NSf = Tile<float>::NSLOT, MBf = Tile<float>::MINB;
+    constexpr int BXd = Tile<double>::BX, NSd = Tile<double>::NSLOT, MBd = Tile<double>::MINB;
+    cudaError_t e;
+    if (esize == 4 && MRTLB_PAIR)
+      e = cudaFuncSetAttribute(step_pair_kernel<BXf, NSf, MRTLB_PAIR_MINB>, A, (int)PairSmem<BXf, NSf>::bytes);
+    else if (esize == 4)
+      e = cudaFuncSetAttribute(step_tiled_kernel<float, BXf, NSf, MBf>, A, (int)Smem<float, BXf, NSf>::bytes);
+    else
+      e = cudaFuncSetAttribute(step_tiled_kernel<double, BXd, NSd, MBd>, A, (int)Smem<double, BXd, NSd>::bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return 4;
+    }
+  }
   plan_segments(L, nsm * per_sm, plan);
   plan->ok = true;
   return 0;
@@ -245,20 +264,10 @@ void launch_step_tiled(const TiledPlan& plan, int cur, const Layout& L, const Co
   dim3 grd(plan.nstrips, plan.nseg);
   if constexpr (sizeof(R) == 4 && MRTLB_PAIR) {
     using SM = PairSmem<BX, NS>;
-    static const bool attr = [] {  // once per instantiation (thread-safe static initialisation)
-      return cudaFuncSetAttribute(step_pair_kernel<BX, NS, MRTLB_PAIR_MINB>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes) == cudaSuccess;
-    }();
-    (void)attr;
     step_pair_kernel<BX, NS, MRTLB_PAIR_MINB><<<grd, BX / 2, SM::bytes, st>>>(
         plan.map[cur], (float*)fout, L, pair_coef(reinterpret_cast<const Coef<float>&>(c)), err, plan.seglen);
   } else {
     using SM = Smem<R, BX, NS>;
-    static const bool attr = [] {
-      return cudaFuncSetAttribute(step_tiled_kernel<R, BX, NS, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)SM::bytes) == cudaSuccess;
-    }();
-    (void)attr;
     step_tiled_kernel<R, BX, NS, MB><<<grd, BX, SM::bytes, st>>>(plan.map[cur], (R*)fout, L, c, err,
                                                                  plan.seglen);
   }
