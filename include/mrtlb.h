@@ -266,7 +266,12 @@ typedef struct mrtlb_batch mrtlb_batch;
 int mrtlb_batch_create(mrtlb_ctx* const* ctxs, int n, mrtlb_batch** out);
 /* Advance every instance by nsteps time steps (asynchronous). */
 int mrtlb_batch_step(mrtlb_batch* b, long nsteps);
-/* Wait for the stream; report a latched device error of batched steps. */
+/* Wait for the stream; report a latched device error of batched steps
+ * (MRTLB_ERR_NONPHYSICAL: some instance met rho <= 0, T <= 0 or a non-finite
+ * value; MRTLB_ERR_TIMEOUT: a bounded wait expired).  The batch has its own
+ * error word, which the instances' calls do not read, and it stays set for
+ * the life of the batch: after re-initialising its instances, make a new
+ * batch. */
 int mrtlb_batch_sync(mrtlb_batch* b);
 /* Tile shape: strip width bx (FP32: 64 or 128; FP64: 64) and rows per
  * segment (>= 1).  The default is the single-grid shape with 32 rows. */
@@ -328,7 +333,10 @@ int mrtlb_get_rates(const mrtlb_ctx* ctx, double* s);
  *   gradients would then mix two runs.  Outputs: dL_ds[16] (host;
  *   entries 5..16 of the paper's s, 0-based 4..15, accumulated in FP64;
  *   0..3 are zero since those rates have no effect) and dL/df^0 (device FP64
- *   [16][ny][nx], or NULL).  Synchronises.
+ *   [16][ny][nx], or NULL).  Synchronises.  A non-physical state met by a
+ *   step of the forward pass (or of its recomputation) makes it return
+ *   MRTLB_ERR_NONPHYSICAL, an expired bounded wait MRTLB_ERR_TIMEOUT; the
+ *   outputs are then meaningless.
  * mrtlb_adjoint_pass(ctx): the id (1, 2, ... per context) of the forward
  *   pass that a backward pass would differentiate now, or 0 when there is
  *   none (no forward pass yet, one that failed, or a context changed since);

@@ -614,6 +614,8 @@ int backward_impl(mrtlb_ctx* c, const double* dL_dmacros, const double* dL_dfK, 
   ACK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, st), "read error word");
   ACK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   if (h & ERRBIT_TIMEOUT) return afail(c, MRTLB_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (h & ERRBIT_NONPHYSICAL)  // (the gradients of such a run mean nothing)
+    return afail(c, MRTLB_ERR_NONPHYSICAL, "a state of the forward pass was non-physical (rho <= 0, T <= 0 or not finite)");
   if (dL_ds)  // the kernels sum the rate gradients without the factor dt
     for (int k = 0; k < 16; ++k) dL_ds[k] *= c->p.dt;
   return MRTLB_OK;

@@ -351,3 +351,21 @@ def test_forward_pass_that_cannot_allocate_keeps_nothing(cuda):
         fresh.adjoint_forward(5)
         _, l2 = fresh.adjoint_backward(dL_dfK=w)
     assert np.array_equal(l1.cpu().numpy(), l2.cpu().numpy())
+
+
+def test_backward_reports_a_nonphysical_forward_pass(cuda):
+    """A forward pass from a state with a negative temperature at one node
+    meets a non-physical state; the backward pass reports it
+    (MRTLB_ERR_NONPHYSICAL) instead of returning gradients of that run."""
+    import torch
+    cfg = _cfg(64, 8, BCS["periodic"], precision="fp32")
+    rho, ux, uy, T = workloads.smooth_fields(cfg.nx, cfg.ny, 190)
+    T[3, 5] = -0.5
+    seed = torch.zeros((4, cfg.ny, cfg.nx), dtype=torch.float64, device=cuda)
+    seed[3] = 1.0
+    with Simulation(cfg) as sim:
+        sim.init_equilibrium(rho, ux, uy, T)
+        sim.adjoint_forward(3)
+        with pytest.raises(M.MrtlbError) as e:
+            sim.adjoint_backward(dL_dmacros=seed)
+        assert e.value.code == M.MRTLB_ERR_NONPHYSICAL

@@ -191,3 +191,25 @@ def test_batch_follows_rates_set_on_an_instance(cuda, precision):
     other = _sims(insts[1:], M.MRTLB_KERNEL_TILED)[0]
     other.step(32)
     assert _rel(other.get_f(), ref[1].get_f()) > 1e-6
+
+
+def test_batch_reports_a_nonphysical_instance(cuda):
+    """A negative temperature in one instance's input makes the batched step
+    latch the non-physical flag, which mrtlb_batch_sync reports
+    (MRTLB_ERR_NONPHYSICAL); the other instance is left as it was stepped."""
+    a, fa = workloads.sod(nx=130, ny=5, precision="fp32")
+    rho, ux, uy, T = (np.array(x, copy=True) for x in fa)
+    T[2, 40] = -0.5
+    s1, s2 = Simulation(a), Simulation(a)
+    s1.init_equilibrium(*fa)
+    s2.init_equilibrium(rho, ux, uy, T)
+    with Batch([s1, s2]) as b:
+        b.step(2)
+        with pytest.raises(M.MrtlbError) as e:
+            b.sync()
+        assert e.value.code == M.MRTLB_ERR_NONPHYSICAL
+    ref = Simulation(a)
+    ref.set_kernel(M.MRTLB_KERNEL_TILED)
+    ref.init_equilibrium(*fa)
+    ref.step(2)
+    assert _rel(s1.get_f(), ref.get_f()) < 1e-6
