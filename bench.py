@@ -24,7 +24,8 @@ Printed JSON line (rank 0):
   small      microseconds per step of the latency-bound small configurations
              (Sod 400 x 4 FP64, Couette 4 x 200 FP64 and FP32)
   cpu_baseline  the FP64 oracle (its plain-C step) on a crop of the same input,
-                one single-threaded process per host core
+                one single-threaded process per host core (and one alone:
+                single_core_mlups)
   oracle_parity the FP32 CUDA path on that crop after the same steps, against
                 the oracle's result (largest errors in rho, u, T)
 
@@ -341,14 +342,23 @@ def cpu_baseline(seconds, dev=None, cores=None):
             return {"error": str(e)[-300:]}, None
         parity = crop_parity(out, ds[0]["steps"], dev) if dev is not None else None
     per = [d["nodes"] * d["timed_steps"] / d["seconds"] / 1e6 for d in ds]
+    # the same step on one core with the others idle (the single-thread rate)
+    single_s = max(1.0, seconds / 5.0)
+    try:
+        d1 = _run_workers(["import bench; bench.cpu_baseline_worker(%r, None, %r, 0)"
+                           % (single_s, time.time() + 3.0)], timeout=300)[0]
+        single = d1["nodes"] * d1["timed_steps"] / d1["seconds"] / 1e6
+    except (RuntimeError, subprocess.SubprocessError):
+        single = None
     x0, y0, nx, ny = CROP
     base = {"value": sum(per), "unit": "MLUPS", "cores": n, "kind": "oracle",
-            "per_core_mlups": sum(per) / n, "cpu_model": cpu_model(),
+            "per_core_mlups": sum(per) / n, "single_core_mlups": single, "cpu_model": cpu_model(),
             "sample": "FP64 oracle (its plain-C step), %d single-threaded processes at once (one per host core), each "
                       "%d-%d timed steps of a %dx%d crop (x %d-%d, y %d-%d) of the Richtmyer-Meshkov 4096x1024 "
-                      "initial state for about %.0f s; value = the sum of their rates"
+                      "initial state for about %.0f s; value = the sum of their rates; single_core_mlups: one "
+                      "such process alone for about %.0f s"
                       % (n, min(d["timed_steps"] for d in ds), max(d["timed_steps"] for d in ds), nx, ny,
-                         x0, x0 + nx - 1, y0, y0 + ny - 1, seconds)}
+                         x0, x0 + nx - 1, y0, y0 + ny - 1, seconds, single_s)}
     return base, parity
 
 

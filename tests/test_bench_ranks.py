@@ -69,3 +69,5 @@ def test_cpu_baseline_runs_one_oracle_process_per_core():
     assert base["cores"] == 2 and base["kind"] == "oracle" and base["value"] > 0
     assert abs(base["per_core_mlups"] * 2 - base["value"]) < 1e-9 * base["value"]
     assert "2 single-threaded processes" in base["sample"]
+    # and one such process alone (the single-thread rate)
+    assert base["single_core_mlups"] > 0
