@@ -19,6 +19,12 @@ Printed JSON line (rank 0):
              its launches, the step kernel being its only kernel), against
              measured HBM copy bandwidth
   fp64_mlups the all-FP64 path on the same input
+  batched    64 seeded uneven instances in one persistent launch per step:
+             MLUPS, fraction of the copy bandwidth at 128 B / node update,
+             and the kernel's DRAM bytes per launch from its ncu summary
+             (traffic, null once the kernel's sources changed)
+  fwd_adj    K = 64 forward + adjoint steps with sqrt(K) checkpoints, and
+             with every state stored, against 320 B / node update
   compute    the step's flop rate (counted flops per node update) against
              fused multiply-add ceilings measured on the device
   small      microseconds per step of the latency-bound small configurations
@@ -187,11 +193,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the step kernel's sources without // comments and blank
-    lines, so that only changes of the code itself invalidate a profile."""
+STEP_SOURCES = ("step_tiled.cu", "march.cuh", "march_pair.cuh", "pair.cuh", "physics.cuh", "kernels.cuh")
+BATCH_SOURCES = ("batch.cu", "march.cuh", "march_pair.cuh", "pair.cuh", "physics.cuh", "kernels.cuh")
+
+
+def kernel_source_hash(names=STEP_SOURCES):
+    """Hash of a kernel's sources without // comments and blank lines, so
+    that only changes of the code itself invalidate a profile."""
     h = hashlib.sha256()
-    for name in ("step_tiled.cu", "march.cuh", "march_pair.cuh", "pair.cuh", "physics.cuh", "kernels.cuh"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_1106_0785_gb300", "csrc", name)) as fh:
             for line in fh:
                 code = re.sub(r"//.*", "", line).strip()
@@ -200,16 +210,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "step_pair_fp32_rm4096x1024.md")
+def profiled_traffic(profile="step_pair_fp32_rm4096x1024.md", names=STEP_SOURCES):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, if
+    it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    if not m or not s or s.group(1) != kernel_source_hash():
+    if not m or not s or s.group(1) != kernel_source_hash(names):
         return None
     return float(m.group(1))
 
@@ -734,6 +744,12 @@ def run_batched(args, world, dev):
            "step_gbs": gbs, "step_frac_of_hbm": gbs / peak,
            "tiles": {"bx": bx, "seglen": seglen, "ntiles": ntiles, "grid": grid},
            "launches_per_step": 2, "graph_steps": 64}
+    # DRAM bytes of one launch of the batched kernel (ncu, its committed
+    # summary, while the kernel's sources hash the same), against the
+    # algorithmic 128 B per node update
+    traffic = profiled_traffic("step_batched_pair_fp32_64instances.md", BATCH_SOURCES)
+    out["traffic"] = traffic
+    out["traffic_over_algorithmic"] = traffic / (BYTES_PER_LUP_FP32 * nodes) if traffic else None
     b.close()
     for s in sims:
         s.close()
