@@ -31,6 +31,9 @@ struct TiledPlan {
 // Encode tensor maps for both buffers and choose strips/segments; returns 0
 // on success (plan->ok set), nonzero if TMA is unavailable (plain path used).
 int plan_tiled(const Layout& L, int esize, void* f0, void* f1, TiledPlan* plan);
+// The automatic kernel choice marches only segments of at least this many
+// rows (shorter ones spend most of their time filling the row pipeline).
+constexpr int kMinMarchRows = 16;
 // Choose a segment length for a target number of CTAs.
 void plan_segments(const Layout& L, int target_ctas, TiledPlan* plan);
 bool tiled_supported(const TiledPlan& plan);
