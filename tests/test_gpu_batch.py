@@ -213,3 +213,41 @@ def test_batch_reports_a_nonphysical_instance(cuda):
     ref.init_equilibrium(*fa)
     ref.step(2)
     assert _rel(s1.get_f(), ref.get_f()) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("bc", ["periodic", "outflow_xy", "walls_y", "reflect_y", "diffuse_x", "inflow"])
+def test_batch_of_degenerate_grids(cuda, bc, precision):
+    """Degenerate grids batched together (a single node, single rows and
+    columns, grids narrower than a column strip or shorter than a row
+    segment, and one ordinary grid beside them), 3 batched steps, each
+    instance against the oracle (FP64 1e-11 per plane; FP32 from the
+    FP32-rounded start, 2e-6 of the state's scale)."""
+    from test_gpu_parity import BCS, _cfg, _input, oracle_params, rel_plane_err
+    shapes = [(1, 1), (2, 3), (1, 6), (7, 1), (3, 130), (129, 2), (300, 5)]
+    cases = []
+    for nx, ny in shapes:
+        if bc == "walls_y" and ny < 3:  # (walls need three nodes across)
+            continue
+        cfg = _cfg(nx, ny, BCS[bc], precision)
+        (rho, ux, uy, T), nz = _input(cfg, 40 + nx + ny)
+        p = oracle_params(cfg)
+        f0 = fdlb.prepare(oeq.feq(rho, ux, uy, T) + nz, p)
+        if precision == "fp32":
+            f0 = f0.astype(np.float32).astype(np.float64)
+        s = Simulation(cfg)
+        s.set_f(f0.astype(np.float32) if precision == "fp32" else f0)
+        cases.append((s, p, f0))
+    with Batch([c[0] for c in cases]) as b:
+        b.step(3)
+        b.sync()
+    for s, p, f0 in cases:
+        g = s.get_f()
+        s.close()
+        assert np.isfinite(g).all()
+        f = fdlb.run(f0, p, 3)
+        if precision == "fp64":
+            assert rel_plane_err(g, f) < 1e-11
+        else:  # against the state's scale: FP32 rounds at the scale of the moments, and a
+            # single node's fast planes (0.004) can be 50x smaller than its largest (0.2)
+            assert np.abs(g - f).max() < 2e-6 * np.abs(f).max()
