@@ -369,3 +369,27 @@ def test_backward_reports_a_nonphysical_forward_pass(cuda):
         with pytest.raises(M.MrtlbError) as e:
             sim.adjoint_backward(dL_dmacros=seed)
         assert e.value.code == M.MRTLB_ERR_NONPHYSICAL
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (1, 6), (7, 1), (3, 130), (129, 2)], ids=lambda s: "%dx%d" % s)
+@pytest.mark.parametrize("bc", ["periodic", "outflow_x", "walls_y", "reflect", "inflow", "diffuse"])
+def test_adjoint_dot_product_on_degenerate_grids(cuda, bc, shape, kernel):
+    """Two adjoint steps on degenerate grids (a single node, single rows and
+    columns, grids narrower than a column strip or shorter than a row
+    segment) through both adjoint kernels: <w, Jv> = <J^T w, v> against the
+    oracle's complex-step tangent (FP64)."""
+    nx, ny = shape
+    cfg = _cfg(nx, ny, BCS[bc])
+    if bc == "walls_y" and ny < 3:  # (walls need three nodes across)
+        with pytest.raises(M.MrtlbError):
+            Simulation(cfg)
+        return
+    f0 = _state(cfg, 200 + nx + ny)
+    rng = np.random.default_rng(201)
+    v = rng.standard_normal(f0.shape)
+    w = rng.standard_normal(f0.shape)
+    _, lam0 = _adjoint(cuda, cfg, f0, 2, w=w, kernel=kernel)
+    Jv = fdlb.run(f0 + 1j * H * v, _oracle_params(cfg), 2).imag / H
+    lhs, rhs = float((w * Jv).sum()), float((lam0 * v).sum())
+    assert abs(lhs - rhs) < 1e-11 * np.abs(w * Jv).sum(), (lhs, rhs)
