@@ -40,3 +40,33 @@ def test_one_step_on_the_tallest_grid(cuda, case, kernel, precision, tol):
 def test_one_row_more_is_rejected(cuda):
     with pytest.raises(M.MrtlbError):
         Simulation(_cfg(NX, NY + 1, BCS["outflow_x"], "fp32"))
+
+
+def test_plane_offsets_beyond_32_bits(cuda):
+    """A grid whose distribution offsets pass 2^31 elements (12288 x 12000
+    nodes: planes of 1.48e8 padded nodes, so plane 15 starts past 2.2e9;
+    9.4 GB per FP32 state): the equilibrium set on the device, one step of
+    the FP32 march, and the nodes nearest the end of the grid plus random
+    ones checked against the oracle's step of their 3 x 3 neighbourhood
+    (the same equilibrium in FP64)."""
+    from paper_1106_0785_gb300 import workloads
+    nx, ny = 12288, 12000
+    cfg, (rho, ux, uy, T) = workloads.richtmyer_meshkov(nx=nx, ny=ny, precision="fp32", dt=5e-6 * 4096 / nx)
+    with Simulation(cfg) as sim:
+        assert sim.state_bytes >= 16 * (ny + 2) * (nx + 2) * 4 and (ny + 2) * (nx + 2) * 15 > 2 ** 31
+        sim.set_kernel(M.MRTLB_KERNEL_TILED)
+        sim.init_equilibrium(rho, ux, uy, T)
+        sim.step(1)
+        out = sim.get_f()
+    rng = np.random.default_rng(9)
+    xs = list(rng.integers(1, nx - 1, 400)) + [nx - 2, nx - 2, nx - 130, 1, 127, 128]
+    ys = list(rng.integers(1, ny - 1, 400)) + [ny - 2, ny - 3, ny - 2, ny - 2, 6000, 11999 - 1]
+    K = len(xs)
+    patch = lambda a: np.concatenate([a[y - 1:y + 2, x - 1:x + 2] for x, y in zip(xs, ys)], axis=1)
+    f = oeq.feq(patch(rho), patch(ux), patch(uy), patch(T))  # (16, 3, 3K)
+    p = oracle_params(cfg)
+    pp = fdlb.Params(nx=3 * K, ny=3, dx=p.dx, dy=p.dy, dt=p.dt, s=p.s, modified=p.modified)
+    ref = fdlb.step(f, pp)[:, 1, 1::3]
+    got = out[:, ys, xs].astype(np.float64)
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    assert (np.abs(got - ref) / scale).max() < 2e-6
