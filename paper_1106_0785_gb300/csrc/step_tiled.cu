@@ -219,22 +219,28 @@ int plan_tiled(const Layout& L, int esize, void* f0, void* f1, TiledPlan* plan) 
       return 4;
     }
   }
-  // One wave of resident CTAs; for the FP32 march two waves when their
-  // segments keep at least kTwoWaveRows rows.  Measured on GB300 (ms per
-  // step, one wave -> two): 4096 x 1024 0.0977 -> 0.0927 (segments of 54 ->
-  // 27 rows), 2048 x 2048 0.0984 -> 0.0949, 4096 x 1536 0.146 -> 0.136,
-  // 4096 x 2048 0.205 -> 0.182, 3072 x 1024 0.0734 -> 0.0720 (21 rows), but
-  // 3000 x 1000 0.0798 -> 0.0810 (20 rows, a ragged last strip); a partial
-  // last wave (1.5 waves: 0.118 on 4096 x 1024) leaves SMs idle.
+  // One wave of resident CTAs; for the FP32 march the most waves, up to
+  // four, whose segments keep at least kWaveRows rows (each wave then marches
+  // a band of rows across the whole width).  Measured on GB300 (ms per step):
+  // 4096 x 1024 0.0977 with one wave -> 0.0927 with two (segments of 54 ->
+  // 27 rows); 2048 x 2048 0.0984 -> 0.0949 (two); 4096 x 1536 0.146 -> 0.136
+  // (two) -> 0.1357 (three); 4096 x 2048 0.205 -> 0.184 (two) -> 0.179
+  // (four); 4096 x 4096 0.382 (two) -> 0.356 (four); 3072 x 1024 0.0734 ->
+  // 0.0720 (21 rows), but 3000 x 1000 0.0798 -> 0.0810 (20 rows, a ragged
+  // last strip); a partial last wave (1.5 waves: 0.118 on 4096 x 1024)
+  // leaves SMs idle.
   plan_segments(L, nsm * per_sm, plan);
   if (esize == 4 && MRTLB_PAIR) {
-    constexpr int kTwoWaveRows = 24;
-    TiledPlan two = *plan;
-    plan_segments(L, 2 * nsm * per_sm, &two);
-    if (two.seglen >= kTwoWaveRows) {
-      plan->nstrips = two.nstrips;
-      plan->nseg = two.nseg;
-      plan->seglen = two.seglen;
+    constexpr int kWaveRows = 24;
+    for (int waves = 4; waves >= 2; --waves) {
+      TiledPlan more = *plan;
+      plan_segments(L, waves * nsm * per_sm, &more);
+      if (more.seglen >= kWaveRows) {
+        plan->nstrips = more.nstrips;
+        plan->nseg = more.nseg;
+        plan->seglen = more.seglen;
+        break;
+      }
     }
   }
   plan->ok = true;
